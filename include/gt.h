@@ -1,0 +1,149 @@
+/*
+ * gt.h -- C-ABI of libgt: edge-tree BFS on one GB300 (sm_103a), after
+ * C. Zhang, "A New Perspective of Graph Data and A Generic and Efficient Method for
+ * Large Scale Graph Data Traversal" (arXiv 2009.07463).
+ *
+ * The library splits a graph into a core subgraph and the edge trees of low-degree
+ * vertices (Sec. 4, Alg. 8), runs direction-optimizing BFS (Alg. 1: top-down queue
+ * expansion, bottom-up scan of unvisited vertices with early exit, a frontier-size
+ * switch) on the core only (Alg. 9, BFS_CORE), then gives every edge-tree vertex its
+ * level and parent from the vertex its tree hangs off (Alg. 10 / Alg. 7).
+ *
+ * Conventions shared by every entry point:
+ *  - Return 0 on success or a negative GT_E* code; gt_strerror() names it and
+ *    gt_last_error() gives a one-line detail of the last failure on this thread.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream). Work is stream-ordered;
+ *    the library never calls cudaDeviceSynchronize. Calls that must read a device
+ *    count back (graph build) synchronise the given stream and say so.
+ *  - Vertex ids are int64 at the boundary and must lie in [0, n); n <= 2^31 - 1.
+ *  - BFS output (Alg. 1 initialisation; Graph500 spanning-tree rule, Sec. 5.3):
+ *    level[v] = hop distance from the root, parent[root] = root, and for every other
+ *    reached v, parent[v] = the smallest vertex id u adjacent to v with
+ *    level[u] = level[v] - 1. Unreached vertices get -1 in both arrays. Self-loops are
+ *    ignored and duplicate tuples merged.
+ *  - The caller owns every buffer it passes; the library owns graph handles and the
+ *    device memory behind them. Handles may be used from one host thread at a time.
+ */
+#ifndef GT_H
+#define GT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GT_API __attribute__((visibility("default")))
+
+/* Status codes. */
+#define GT_OK 0
+#define GT_EINVAL (-1)   /* bad argument: null pointer, id out of range, bad size */
+#define GT_ENOMEM (-2)   /* device or host allocation failed */
+#define GT_ETIMEOUT (-3) /* a bounded wait ran out */
+#define GT_EBUSY (-4)    /* resource in use */
+#define GT_EDEVICE (-5)  /* CUDA error (detail in gt_last_error) */
+#define GT_ENOTSUP (-6)  /* not supported on this device / build */
+
+/* Vertex classes of Sec. 4.2 (codes of gt_graph_vertex_type). */
+#define GT_CORE_INTERNAL 0 /* CI */
+#define GT_CORE_EDGE 1     /* CE */
+#define GT_TREE_INTERNAL 2 /* TI */
+#define GT_TREE_LEAF 3     /* TL */
+#define GT_VERTEX_ZERO 4   /* VZ */
+
+/* Build-time options. */
+typedef struct gt_config {
+  int32_t mh;         /* maximum edge-tree height MH of Alg. 8: 0 = leaves only (default,
+                         the paper's choice in Sec. 6.2), -1 = peel to the fixpoint */
+  int32_t keep_plain; /* 1 (default): keep the unsplit CSR and its BFS state so
+                         gt_bfs_plain works; 0: free them after the split */
+} gt_config;
+
+/* Run-time tuning of the traversal; results never depend on it. */
+typedef struct gt_tuning {
+  int32_t alpha;        /* top-down -> bottom-up when m_f * alpha > m_u (default 14) */
+  int32_t beta;         /* bottom-up -> top-down when n_f * beta < n and shrinking (24) */
+  int32_t td_warp_min;  /* top-down: degree above which a whole warp takes a vertex (32) */
+  int32_t td_grid_min;  /* top-down: degree above which all CTAs share a vertex (4096) */
+  int32_t bu_thread_scan; /* bottom-up: neighbours a lane checks alone before the warp
+                             takes the vertex over (8) */
+  int32_t blocks_per_sm;  /* CTAs per SM of the traversal kernels (4) */
+  int32_t force_direction; /* 0 = switch heuristic, 1 = top-down only, 2 = bottom-up only */
+  int32_t launch_mode;  /* 0 = whole level loop in one CUDA graph with device-side
+                           control (default), 1 = host-driven loop (one readback per level) */
+  int32_t count_work;   /* 1: count examined edges per level (slower; for the trace) */
+} gt_tuning;
+
+typedef struct gt_stats {
+  int64_t n;          /* vertices */
+  int64_t m;          /* input tuples */
+  int64_t nnz;        /* directed adjacency entries after cleanup (2 x undirected edges) */
+  int64_t n_core;     /* CI + CE */
+  int64_t nnz_core;   /* directed core-to-core entries */
+  int64_t n_class[5]; /* counts of CI, CE, TI, TL, VZ */
+  int32_t mh;         /* MH used */
+  int32_t height;     /* largest height h at which Alg. 8 marked a tree-internal vertex */
+  int64_t device_bytes; /* device memory held by the handle */
+} gt_stats;
+
+/* One level of the last traversal on a handle (bfs trace). */
+typedef struct gt_level_info {
+  int32_t level;        /* level of the frontier this step expanded */
+  int32_t direction;    /* 0 top-down, 1 bottom-up */
+  int64_t frontier;     /* frontier vertices n_f */
+  int64_t frontier_edges; /* sum of their degrees m_f */
+  int64_t unvisited_edges; /* m_u before the step */
+  int64_t discovered;   /* vertices found by the step */
+  int64_t examined;     /* adjacency entries read by the step (count_work = 1), else -1 */
+} gt_level_info;
+
+typedef struct gt_graph* gt_graph_t;
+
+GT_API void gt_config_default(gt_config* cfg);
+GT_API void gt_tuning_default(gt_tuning* t);
+
+/* Build a graph handle from m tuples (edges[2i], edges[2i+1]), host or device memory
+ * (int64, 16-byte aligned if on the device), over vertices [0, n).
+ * Steps (all on the device): symmetrise, radix-sort the packed (u, v) keys, drop
+ * self-loops and duplicates, row offsets by scan (Sec. 5.1.1 CSR); classify vertices
+ * with Alg. 8 at MH = cfg->mh (Sec. 4.3); relabel the core (CI + CE) monotonically in
+ * vertex id (the core-left layout of Sec. 5.1.1) and compact core-to-core edges into a
+ * dense int32 CSR; lay out the edge-tree edge list (Sec. 5.1.2).
+ * cfg may be NULL (defaults). Synchronises `stream`. Returns GT_EINVAL if a tuple has
+ * an id outside [0, n) (nothing is kept), GT_ENOMEM if device memory runs out. */
+GT_API int gt_graph_build(const int64_t* edges, int64_t m, int64_t n, const gt_config* cfg, void* stream,
+                          gt_graph_t* out);
+GT_API void gt_graph_free(gt_graph_t g);
+GT_API int gt_graph_stats(gt_graph_t g, gt_stats* out);
+/* Copy Alg. 8's vertex_type[n] (GT_* class codes) into out (host or device). */
+GT_API int gt_graph_vertex_type(gt_graph_t g, uint8_t* out, void* stream);
+/* Copy the cleaned degree of every vertex (int32[n]) into out (host or device). */
+GT_API int gt_graph_degree(gt_graph_t g, int32_t* out, void* stream);
+GT_API int gt_graph_get_tuning(gt_graph_t g, gt_tuning* out);
+GT_API int gt_graph_set_tuning(gt_graph_t g, const gt_tuning* t);
+
+/* Edge-tree BFS from `root` (Alg. 9): root-in-tree walk to its core vertex, BFS on the
+ * core only, then edge-tree resolution. parent and level are int32[n], both device or
+ * both host memory; with host memory the call copies the result back and returns after
+ * `stream` has finished. */
+GT_API int gt_bfs(gt_graph_t g, int64_t root, int32_t* parent, int32_t* level, void* stream);
+/* The same contract on the unsplit graph (plain direction-optimizing BFS, Alg. 1); the
+ * comparison baseline. GT_ENOTSUP if the handle was built with keep_plain = 0. */
+GT_API int gt_bfs_plain(gt_graph_t g, int64_t root, int32_t* parent, int32_t* level, void* stream);
+/* Per-level trace of the last gt_bfs / gt_bfs_plain on g (synchronises the stream it
+ * ran on). Writes up to cap entries, *nlevels = levels run. */
+GT_API int gt_bfs_trace(gt_graph_t g, gt_level_info* out, int32_t cap, int32_t* nlevels);
+
+/* Graph500 TEPS numerator: number of tuples (device int64[m][2], 16-byte aligned) whose
+ * two ends both have level >= 0 (device int32 level[n]). Synchronises `stream`.
+ * GT_EINVAL if a tuple holds an id outside [0, n) (nothing is read out of bounds). */
+GT_API int gt_count_traversed(const int64_t* edges, int64_t m, const int32_t* level, int64_t n, int64_t* out,
+                              void* stream);
+
+GT_API const char* gt_strerror(int code);
+GT_API const char* gt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GT_H */

@@ -1,0 +1,262 @@
+"""Edge-tree BFS on GB300 (arXiv 2009.07463): thin Python binding over libgt (include/gt.h).
+
+The functions here carry the C-ABI's names and only marshal arguments: every step of the
+path runs in the library's CUDA kernels. Buffers may be torch tensors (device or host),
+numpy arrays (host) or raw integer pointers; streams are torch streams or raw handles.
+There is no CPU fallback: if libgt.so cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import native
+
+GT_OK, GT_EINVAL, GT_ENOMEM, GT_ETIMEOUT, GT_EBUSY, GT_EDEVICE, GT_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+CORE_INTERNAL, CORE_EDGE, TREE_INTERNAL, TREE_LEAF, VERTEX_ZERO = 0, 1, 2, 3, 4
+
+
+class gt_config(ctypes.Structure):
+    _fields_ = [("mh", ctypes.c_int32), ("keep_plain", ctypes.c_int32)]
+
+
+class gt_tuning(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in (
+        "alpha", "beta", "td_warp_min", "td_grid_min", "bu_thread_scan", "blocks_per_sm",
+        "force_direction", "launch_mode", "count_work")]
+
+
+class gt_stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("n_core", ctypes.c_int64), ("nnz_core", ctypes.c_int64), ("n_class", ctypes.c_int64 * 5),
+                ("mh", ctypes.c_int32), ("height", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+
+
+class gt_level_info(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int32), ("direction", ctypes.c_int32), ("frontier", ctypes.c_int64),
+                ("frontier_edges", ctypes.c_int64), ("unvisited_edges", ctypes.c_int64),
+                ("discovered", ctypes.c_int64), ("examined", ctypes.c_int64)]
+
+
+class GtError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str):
+        super().__init__(f"{where}: {detail or 'error'} (status {code})")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """The loaded libgt (built in-tree on first use)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = native.build()
+            L = ctypes.CDLL(path)
+            p, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+            sig = {
+                "gt_config_default": (None, [p]),
+                "gt_tuning_default": (None, [p]),
+                "gt_graph_build": (ctypes.c_int, [p, i64, i64, p, p, p]),
+                "gt_graph_free": (None, [p]),
+                "gt_graph_stats": (ctypes.c_int, [p, p]),
+                "gt_graph_vertex_type": (ctypes.c_int, [p, p, p]),
+                "gt_graph_degree": (ctypes.c_int, [p, p, p]),
+                "gt_graph_get_tuning": (ctypes.c_int, [p, p]),
+                "gt_graph_set_tuning": (ctypes.c_int, [p, p]),
+                "gt_bfs": (ctypes.c_int, [p, i64, p, p, p]),
+                "gt_bfs_plain": (ctypes.c_int, [p, i64, p, p, p]),
+                "gt_bfs_trace": (ctypes.c_int, [p, p, i32, p]),
+                "gt_count_traversed": (ctypes.c_int, [p, i64, p, i64, p, p]),
+                "gt_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+                "gt_last_error": (ctypes.c_char_p, []),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc: int, where: str):
+    if rc != GT_OK:
+        raise GtError(rc, where, lib().gt_last_error().decode())
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _stream(s) -> int:
+    if s is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return 0
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _len_pairs(edges) -> int:
+    shape = tuple(edges.shape)
+    if len(shape) != 2 or shape[1] != 2:
+        raise ValueError("edges must have shape [m, 2]")
+    return int(shape[0])
+
+
+def tuning_default() -> gt_tuning:
+    t = gt_tuning()
+    lib().gt_tuning_default(ctypes.byref(t))
+    return t
+
+
+class Graph:
+    """A graph handle: device CSR, core CSR, edge-tree layout and traversal state."""
+
+    def __init__(self, handle: int, n: int):
+        self._h = handle
+        self.n = n
+
+    @property
+    def handle(self) -> int:
+        return self._h
+
+    def free(self):
+        if self._h:
+            lib().gt_graph_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def stats(self) -> dict:
+        st = gt_stats()
+        _check(lib().gt_graph_stats(self._h, ctypes.byref(st)), "gt_graph_stats")
+        return {"n": st.n, "m": st.m, "nnz": st.nnz, "n_core": st.n_core, "nnz_core": st.nnz_core,
+                "n_class": list(st.n_class), "mh": st.mh, "height": st.height, "device_bytes": st.device_bytes}
+
+    def vertex_type(self, out=None, stream=None):
+        out = np.empty(self.n, dtype=np.uint8) if out is None else out
+        _check(lib().gt_graph_vertex_type(self._h, _ptr(out), _stream(stream)), "gt_graph_vertex_type")
+        return out
+
+    def degree(self, out=None, stream=None):
+        out = np.empty(self.n, dtype=np.int32) if out is None else out
+        _check(lib().gt_graph_degree(self._h, _ptr(out), _stream(stream)), "gt_graph_degree")
+        return out
+
+    def get_tuning(self) -> gt_tuning:
+        t = gt_tuning()
+        _check(lib().gt_graph_get_tuning(self._h, ctypes.byref(t)), "gt_graph_get_tuning")
+        return t
+
+    def set_tuning(self, t: gt_tuning | None = None, **kw):
+        t = self.get_tuning() if t is None else t
+        for k, v in kw.items():
+            setattr(t, k, int(v))
+        _check(lib().gt_graph_set_tuning(self._h, ctypes.byref(t)), "gt_graph_set_tuning")
+
+    def bfs(self, root: int, parent=None, level=None, stream=None, plain: bool = False):
+        """Levels and min-id parents from root; host numpy outputs when none are given."""
+        if parent is None and level is None:
+            parent = np.empty(self.n, dtype=np.int32)
+            level = np.empty(self.n, dtype=np.int32)
+        f = lib().gt_bfs_plain if plain else lib().gt_bfs
+        _check(f(self._h, int(root), _ptr(parent), _ptr(level), _stream(stream)),
+               "gt_bfs_plain" if plain else "gt_bfs")
+        return parent, level
+
+    def bfs_plain(self, root: int, parent=None, level=None, stream=None):
+        return self.bfs(root, parent, level, stream, plain=True)
+
+    def trace(self) -> list[dict]:
+        cap = 4096
+        arr = (gt_level_info * cap)()
+        nl = ctypes.c_int32(0)
+        _check(lib().gt_bfs_trace(self._h, arr, cap, ctypes.byref(nl)), "gt_bfs_trace")
+        out = []
+        for i in range(min(nl.value, cap)):
+            t = arr[i]
+            out.append({"level": t.level, "direction": "bu" if t.direction else "td", "frontier": t.frontier,
+                        "frontier_edges": t.frontier_edges, "unvisited_edges": t.unvisited_edges,
+                        "discovered": t.discovered, "examined": t.examined})
+        return out
+
+
+def gt_graph_build(edges, n: int, mh: int = 0, keep_plain: bool = True, stream=None, m: int | None = None) -> Graph:
+    """Build a graph handle from int64 tuples [m, 2] (numpy/torch host or torch device, or a pointer + m)."""
+    if m is None:
+        m = _len_pairs(edges)
+    cfg = gt_config(mh=int(mh), keep_plain=int(bool(keep_plain)))
+    h = ctypes.c_void_p()
+    _check(lib().gt_graph_build(_ptr(edges), int(m), int(n), ctypes.byref(cfg), _stream(stream), ctypes.byref(h)),
+           "gt_graph_build")
+    return Graph(h.value, int(n))
+
+
+def gt_graph_free(g: Graph):
+    g.free()
+
+
+def gt_graph_stats(g: Graph) -> dict:
+    return g.stats()
+
+
+def gt_graph_vertex_type(g: Graph, out=None, stream=None):
+    return g.vertex_type(out, stream)
+
+
+def gt_graph_degree(g: Graph, out=None, stream=None):
+    return g.degree(out, stream)
+
+
+def gt_graph_set_tuning(g: Graph, t: gt_tuning | None = None, **kw):
+    g.set_tuning(t, **kw)
+
+
+def gt_graph_get_tuning(g: Graph) -> gt_tuning:
+    return g.get_tuning()
+
+
+def gt_bfs(g: Graph, root: int, parent=None, level=None, stream=None):
+    return g.bfs(root, parent, level, stream)
+
+
+def gt_bfs_plain(g: Graph, root: int, parent=None, level=None, stream=None):
+    return g.bfs_plain(root, parent, level, stream)
+
+
+def gt_bfs_trace(g: Graph) -> list[dict]:
+    return g.trace()
+
+
+def gt_count_traversed(edges, level, stream=None, m: int | None = None) -> int:
+    """Tuples (device int64 [m, 2]) with both ends reached (device int32 level)."""
+    if m is None:
+        m = _len_pairs(edges)
+    out = ctypes.c_int64(0)
+    n = int(level.numel() if hasattr(level, "numel") else len(level))
+    _check(lib().gt_count_traversed(_ptr(edges), int(m), _ptr(level), n, ctypes.byref(out), _stream(stream)),
+           "gt_count_traversed")
+    return int(out.value)

@@ -1,0 +1,308 @@
+// capi.cu -- the extern "C" entry points declared in include/gt.h: argument checks,
+// host/device buffer handling, status codes. All compute happens in the kernels of
+// build.cu and bfs.cu.
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "gt_device.cuh"
+#include "gt_internal.cuh"
+
+namespace gt {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& s) { g_last_error = s; }
+
+int cuda_fail(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return GT_OK;
+  cudaGetLastError();
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? GT_ENOMEM : GT_EDEVICE;
+}
+
+namespace {
+
+int select_device(cudaStream_t s, int* dev) {
+  int d = 0;
+  if (s) {
+    if (cudaStreamGetDevice(s, &d) != cudaSuccess) {
+      cudaGetLastError();
+      if (cudaGetDevice(&d) != cudaSuccess) return cuda_fail(cudaGetLastError(), "cudaGetDevice");
+    }
+  } else if (cudaGetDevice(&d) != cudaSuccess) {
+    return cuda_fail(cudaGetLastError(), "cudaGetDevice");
+  }
+  if (dev) *dev = d;
+  return cuda_fail(cudaSetDevice(d), "cudaSetDevice");
+}
+
+// 1: device (or managed) memory, 0: host memory, -1: null
+int where(const void* p) {
+  if (!p) return -1;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? 1 : 0;
+}
+
+void apply_launch(gt_graph* g) {
+  int bpm = g->tuning.blocks_per_sm > 0 ? g->tuning.blocks_per_sm : 4;
+  g->launch.grid = g->launch.sms * bpm;
+}
+
+__global__ void count_traversed(const int64_t* __restrict__ edges, int64_t m, const int32_t* __restrict__ level,
+                                int64_t n, unsigned long long* __restrict__ out, int* __restrict__ bad) {
+  unsigned long long c = 0;
+  for (int64_t i = gtid(); i < m; i += gthreads()) {
+    const longlong2 e = reinterpret_cast<const longlong2*>(edges)[i];
+    if (e.x < 0 || e.x >= n || e.y < 0 || e.y >= n) {
+      *bad = 1;
+      continue;
+    }
+    c += (level[e.x] >= 0) & (level[e.y] >= 0);
+  }
+  c = warp_sum(c);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+int bfs_common(gt_graph_t g, bool et, int64_t root, int32_t* parent, int32_t* level, void* stream) {
+  if (!g || !parent || !level) {
+    set_error("gt_bfs: null handle or output");
+    return GT_EINVAL;
+  }
+  if (root < 0 || root >= g->n) {
+    set_error("gt_bfs: root outside [0, n)");
+    return GT_EINVAL;
+  }
+  if (!et && !g->cfg.keep_plain) {
+    set_error("gt_bfs_plain: handle built with keep_plain = 0");
+    return GT_ENOTSUP;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = cuda_fail(cudaSetDevice(g->device), "cudaSetDevice");
+  if (rc) return rc;
+  const int wp = where(parent), wl = where(level);
+  if (wp != wl) {
+    set_error("gt_bfs: parent and level must both be device or both host memory");
+    return GT_EINVAL;
+  }
+  gt::View& v = et ? g->core : g->plain;
+  if (wp == 1) return run_bfs(g, v, et, root, parent, level, s);
+  if (!g->scratch_out) {
+    rc = device_malloc(g, (void**)&g->scratch_out, sizeof(int32_t) * 2 * g->n);
+    if (rc) return rc;
+  }
+  int32_t* dp = g->scratch_out;
+  int32_t* dl = g->scratch_out + g->n;
+  rc = run_bfs(g, v, et, root, dp, dl, s);
+  if (rc) return rc;
+  rc = cuda_fail(cudaMemcpyAsync(parent, dp, sizeof(int32_t) * g->n, cudaMemcpyDeviceToHost, s), "copy parent");
+  if (!rc) rc = cuda_fail(cudaMemcpyAsync(level, dl, sizeof(int32_t) * g->n, cudaMemcpyDeviceToHost, s), "copy level");
+  if (!rc) rc = cuda_fail(cudaStreamSynchronize(s), "bfs sync");
+  return rc;
+}
+
+int copy_out(gt_graph_t g, void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  int rc = cuda_fail(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s), "copy");
+  if (!rc && where(dst) == 0) rc = cuda_fail(cudaStreamSynchronize(s), "sync");
+  (void)g;
+  return rc;
+}
+
+}  // namespace
+}  // namespace gt
+
+using namespace gt;
+
+extern "C" {
+
+GT_API void gt_config_default(gt_config* c) {
+  if (!c) return;
+  memset(c, 0, sizeof(*c));
+  c->mh = 0;
+  c->keep_plain = 1;
+}
+
+GT_API void gt_tuning_default(gt_tuning* t) {
+  if (!t) return;
+  memset(t, 0, sizeof(*t));
+  t->alpha = 14;
+  t->beta = 24;
+  t->td_warp_min = 32;
+  t->td_grid_min = 4096;
+  t->bu_thread_scan = 8;
+  t->blocks_per_sm = 4;
+  t->force_direction = 0;
+  t->launch_mode = 0;
+  t->count_work = 0;
+}
+
+GT_API int gt_graph_build(const int64_t* edges, int64_t m, int64_t n, const gt_config* cfg, void* stream,
+                          gt_graph_t* out) {
+  if (!out || (m > 0 && !edges) || m < 0 || n < 1 || n > 0x7FFFFFFFLL) {
+    set_error("gt_graph_build: need out != NULL, edges != NULL when m > 0, m >= 0, 1 <= n <= 2^31 - 1");
+    return GT_EINVAL;
+  }
+  if (cfg && cfg->mh < -1) {
+    set_error("gt_graph_build: mh must be >= -1");
+    return GT_EINVAL;
+  }
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0;
+  int rc = select_device(s, &dev);
+  if (rc) return rc;
+  gt_graph* g = new (std::nothrow) gt_graph();
+  if (!g) return GT_ENOMEM;
+  g->device = dev;
+  if (cfg)
+    g->cfg = *cfg;
+  else
+    gt_config_default(&g->cfg);
+  gt_tuning_default(&g->tuning);
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  g->launch.sms = sms > 0 ? sms : 1;
+  apply_launch(g);
+  rc = build_graph(g, edges, m, n, s);
+  if (rc) {
+    cudaStreamSynchronize(s);
+    cudaGetLastError();
+    free_graph(g);
+    delete g;
+    return rc;
+  }
+  *out = g;
+  return GT_OK;
+}
+
+GT_API void gt_graph_free(gt_graph_t g) {
+  if (!g) return;
+  cudaSetDevice(g->device);
+  if (g->last_stream) cudaStreamSynchronize(g->last_stream);
+  free_graph(g);
+  delete g;
+}
+
+GT_API int gt_graph_stats(gt_graph_t g, gt_stats* out) {
+  if (!g || !out) return GT_EINVAL;
+  *out = g->stats;
+  out->device_bytes = g->device_bytes;
+  return GT_OK;
+}
+
+GT_API int gt_graph_vertex_type(gt_graph_t g, uint8_t* out, void* stream) {
+  if (!g || !out) return GT_EINVAL;
+  cudaSetDevice(g->device);
+  return copy_out(g, out, g->vtype, (size_t)g->n, (cudaStream_t)stream);
+}
+
+GT_API int gt_graph_degree(gt_graph_t g, int32_t* out, void* stream) {
+  if (!g || !out) return GT_EINVAL;
+  cudaSetDevice(g->device);
+  return copy_out(g, out, g->deg, sizeof(int32_t) * (size_t)g->n, (cudaStream_t)stream);
+}
+
+GT_API int gt_graph_get_tuning(gt_graph_t g, gt_tuning* out) {
+  if (!g || !out) return GT_EINVAL;
+  *out = g->tuning;
+  return GT_OK;
+}
+
+GT_API int gt_graph_set_tuning(gt_graph_t g, const gt_tuning* t) {
+  if (!g || !t) return GT_EINVAL;
+  if (t->alpha < 1 || t->beta < 1 || t->td_warp_min < 1 || t->td_grid_min < t->td_warp_min ||
+      t->bu_thread_scan < 0 || t->blocks_per_sm < 1 || t->blocks_per_sm > 32 || t->force_direction < 0 ||
+      t->force_direction > 2 || t->launch_mode < 0 || t->launch_mode > 1) {
+    set_error("gt_graph_set_tuning: value out of range");
+    return GT_EINVAL;
+  }
+  cudaSetDevice(g->device);
+  if (g->last_stream) cudaStreamSynchronize(g->last_stream);
+  g->tuning = *t;
+  apply_launch(g);
+  for (int i = 0; i < 2; ++i) {
+    if (g->loop_exec[i]) cudaGraphExecDestroy(g->loop_exec[i]);
+    g->loop_exec[i] = nullptr;
+  }
+  return GT_OK;
+}
+
+GT_API int gt_bfs(gt_graph_t g, int64_t root, int32_t* parent, int32_t* level, void* stream) {
+  return bfs_common(g, true, root, parent, level, stream);
+}
+
+GT_API int gt_bfs_plain(gt_graph_t g, int64_t root, int32_t* parent, int32_t* level, void* stream) {
+  return bfs_common(g, false, root, parent, level, stream);
+}
+
+GT_API int gt_bfs_trace(gt_graph_t g, gt_level_info* out, int32_t cap, int32_t* nlevels) {
+  if (!g || !nlevels || cap < 0 || (cap > 0 && !out)) return GT_EINVAL;
+  *nlevels = 0;
+  if (!g->last_ctl) return GT_OK;
+  cudaSetDevice(g->device);
+  int rc = cuda_fail(cudaStreamSynchronize(g->last_stream), "trace sync");
+  if (rc) return rc;
+  int32_t nl = 0;
+  rc = cuda_fail(cudaMemcpy(&nl, &g->last_ctl->nlevels, sizeof(int32_t), cudaMemcpyDeviceToHost), "trace");
+  if (rc) return rc;
+  *nlevels = nl;
+  int32_t k = nl < cap ? nl : cap;
+  if (k > MAX_TRACE) k = MAX_TRACE;
+  if (k > 0)
+    rc = cuda_fail(cudaMemcpy(out, g->last_ctl->trace, sizeof(gt_level_info) * k, cudaMemcpyDeviceToHost), "trace");
+  return rc;
+}
+
+GT_API int gt_count_traversed(const int64_t* edges, int64_t m, const int32_t* level, int64_t n, int64_t* out,
+                              void* stream) {
+  if (!out || m < 0 || n < 0 || (m > 0 && (!edges || !level))) return GT_EINVAL;
+  *out = 0;
+  if (m == 0) return GT_OK;
+  if ((uintptr_t)edges & 15) {
+    set_error("gt_count_traversed: tuples must be 16-byte aligned device memory");
+    return GT_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = select_device(s, nullptr);
+  if (rc) return rc;
+  unsigned long long* d = nullptr;
+  rc = cuda_fail(cudaMallocAsync((void**)&d, 2 * sizeof(unsigned long long), s), "alloc");
+  if (rc) return rc;
+  cudaMemsetAsync(d, 0, 2 * sizeof(unsigned long long), s);
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  count_traversed<<<sms * 8, 256, 0, s>>>(edges, m, level, n, d, (int*)(d + 1));
+  unsigned long long h[2] = {0, 0};
+  rc = cuda_fail(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s), "count readback");
+  cudaFreeAsync(d, s);
+  if (!rc) rc = cuda_fail(cudaStreamSynchronize(s), "count sync");
+  if (!rc && h[1]) {
+    set_error("gt_count_traversed: a tuple has a vertex id outside [0, n)");
+    return GT_EINVAL;
+  }
+  *out = (int64_t)h[0];
+  return rc;
+}
+
+GT_API const char* gt_strerror(int code) {
+  switch (code) {
+    case GT_OK: return "ok";
+    case GT_EINVAL: return "invalid argument";
+    case GT_ENOMEM: return "out of memory";
+    case GT_ETIMEOUT: return "timed out";
+    case GT_EBUSY: return "busy";
+    case GT_EDEVICE: return "CUDA error";
+    case GT_ENOTSUP: return "not supported";
+    default: return "unknown error";
+  }
+}
+
+GT_API const char* gt_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

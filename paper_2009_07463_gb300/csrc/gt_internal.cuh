@@ -1,0 +1,129 @@
+// gt_internal.cuh -- definitions shared by the translation units of libgt.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "gt.h"
+
+namespace gt {
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+constexpr uint64_t UNVISITED = ~0ull;   // packed (level << 32 | parent) of an unvisited vertex
+constexpr int DIR_TD = 0, DIR_BU = 1;
+constexpr int MAX_TRACE = 4096;
+constexpr int BFS_THREADS = 256;
+constexpr int BU_CHUNK_WORDS = 128;     // bitmap words one warp takes per step (4096 vertices)
+
+// Per-traversal control block in device memory. Kernels read the direction and buffer
+// selectors from here, so the level loop can run without the host (CUDA graph with a
+// device-set while condition) or with one small readback per level.
+struct BfsCtl {
+  int32_t level;      // level of the current frontier
+  int32_t dir;        // direction of the step now due
+  int32_t done;       // 1 when the frontier is empty
+  int32_t cur;        // queue holding the current frontier (0/1)
+  int32_t vcur;       // visited bitmap that is current (0/1)
+  int32_t need_mark;  // 1: set visited bits of the current queue before a bottom-up step
+  int32_t nlevels;    // steps taken
+  int32_t err;        // nonzero: a kernel found an inconsistency
+  int64_t n_f;        // current frontier vertices
+  int64_t m_f;        // their summed degree
+  int64_t prev_n_f;
+  int64_t m_u;        // summed degree of unvisited vertices
+  int64_t next_n;     // accumulators of the step in progress
+  int64_t next_m;
+  int64_t examined;
+  int64_t big_n;      // top-down: vertices handed to the whole grid
+  // traversal start (set by the start kernel)
+  int32_t start;      // start vertex in the traversed graph's ids (-1: nothing to traverse)
+  int32_t start_level;
+  int32_t alpha, beta, force;
+  int32_t pad0;
+  gt_level_info trace[MAX_TRACE];
+};
+
+// A graph the level loop traverses: the core CSR (edge-tree BFS) or the full CSR (plain).
+struct View {
+  int64_t n = 0;        // vertices
+  int64_t nnz = 0;      // directed entries
+  int64_t nwords = 0;   // bitmap words, padded to a multiple of BU_CHUNK_WORDS
+  int64_t* row = nullptr;
+  int32_t* col = nullptr;
+  uint64_t* state = nullptr;   // packed level/parent per vertex
+  uint32_t* vis[2] = {nullptr, nullptr};
+  int32_t* queue[2] = {nullptr, nullptr};
+  int32_t* big = nullptr;      // top-down vertices shared by the whole grid
+  BfsCtl* ctl = nullptr;
+};
+
+struct LaunchCfg {
+  int sms = 152;
+  int grid = 608;
+};
+
+}  // namespace gt
+
+struct gt_graph {
+  int device = 0;
+  int64_t n = 0, m = 0, nnz = 0;
+  gt_config cfg{};
+  gt_tuning tuning{};
+  gt_stats stats{};
+  gt::LaunchCfg launch{};
+  // full CSR (Sec. 5.1.1)
+  int64_t* row = nullptr;
+  int32_t* col = nullptr;
+  int32_t* deg = nullptr;       // cleaned degree per vertex
+  uint8_t* vtype = nullptr;     // Alg. 8 classes
+  int32_t* up = nullptr;        // edge-tree vertex -> the neighbour it hangs from (-1 top / none)
+  int32_t* vinfo = nullptr;     // >= 0 core id; <= -2: tree vertex whose up is core id (-2 - x); -1 other
+  int32_t* new2old = nullptr;   // core id -> vertex id
+  int32_t* old2core = nullptr;  // vertex id -> core id or -1
+  int32_t* epoch = nullptr;     // root-path marks for the tree-up resolution pass
+  int32_t* resolve_list = nullptr;  // tree vertices whose up is a tree vertex, by height desc
+  int32_t* resolve_up = nullptr;
+  int64_t* resolve_ptr_host = nullptr;  // segment starts per height (host copy), nheights + 1
+  int32_t resolve_heights = 0;
+  int64_t resolve_n = 0;
+  int32_t cur_epoch = 0;
+  gt::View core;   // core CSR + traversal state
+  gt::View plain;  // full CSR + traversal state (keep_plain)
+  int32_t* scratch_out = nullptr;  // device staging when the caller passes host outputs
+  cudaStream_t last_stream = nullptr;
+  gt::BfsCtl* last_ctl = nullptr;
+  // CUDA graphs of the level loop, one per view, instantiated lazily
+  cudaGraphExec_t loop_exec[2] = {nullptr, nullptr};
+  int64_t device_bytes = 0;
+};
+
+namespace gt {
+
+// error reporting (capi.cu)
+void set_error(const std::string& s);
+int cuda_fail(cudaError_t e, const char* what);
+
+// build.cu
+int build_graph(gt_graph* g, const int64_t* edges, int64_t m, int64_t n, cudaStream_t s);
+int alloc_view_state(gt_graph* g, View& v, cudaStream_t s);
+void free_graph(gt_graph* g);
+int device_malloc(gt_graph* g, void** p, size_t bytes);
+
+// scan.cu
+// out[i] = sum_{j < i} in[j] for i in [0, n]; out has n + 1 entries.
+int scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s, void* tmp, size_t tmp_bytes);
+size_t scan_tmp_bytes(int64_t n);
+// as above for u8 flags -> int32 exclusive positions (n + 1 entries), total < 2^31
+int scan_u8_to_i32(const uint8_t* in, int32_t* out, int64_t n, cudaStream_t s, void* tmp, size_t tmp_bytes);
+
+// radix.cu
+size_t radix_tmp_bytes(int64_t nkeys, int grid);
+// LSD radix sort of u64 keys on their low `bits` bits; result ends in *keys (ping-pong with alt).
+int radix_sort_u64(uint64_t** keys, uint64_t** alt, int64_t nkeys, int bits, int grid, void* tmp,
+                   cudaStream_t s);
+
+// bfs.cu
+int run_bfs(gt_graph* g, View& v, bool et, int64_t root, int32_t* parent, int32_t* level, cudaStream_t s);
+
+}  // namespace gt
