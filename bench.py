@@ -1,0 +1,466 @@
+#!/usr/bin/env python
+"""Benchmark: harmonic-mean GTEPS of edge-tree BFS over 64 roots on R-MAT scale 26.
+
+One step = one single-root edge-tree BFS (gt_bfs) from each of the 64 seeded roots, each
+timed on its own with CUDA events on the launching stream, inputs resident in HBM (the
+graph is built once, untimed, as Graph500 excludes construction). GTEPS of a run = input
+tuples with both ends reached / its time; value = harmonic mean over all timed runs
+(times the number of replicas for N > 1: every GPU holds a full replica and takes its own
+64 roots, so per-GPU work is fixed and scaling is weak).
+
+Also measured, outside the timed region: the plain direction-optimizing BFS on the unsplit
+graph (same roots), the end-to-end number through the C-ABI with host output buffers,
+the roofline of the bottom-up kernel (durations from CUDA events around each launch in a
+kernel-timing pass, algorithmic bytes from the per-level work counts), and the CPU oracle
+on a bounded sample of the same workload.
+
+--impl reference times the CPU oracle itself (serial BFS, the checker the tests use) on
+the same workload, one root per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import multiprocessing as mp
+import os
+import re
+import signal
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "harmonic-mean GTEPS over 64 roots at R-MAT scale 26; served queries/s and p99"
+UNIT = "GTEPS"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=int, default=26)
+    ap.add_argument("--edgefactor", type=int, default=16)
+    ap.add_argument("--roots", type=int, default=64)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--root-seed", type=int, default=2)
+    ap.add_argument("--mh", type=int, default=0)
+    ap.add_argument("--cpu-baseline", default="on", choices=["on", "off"])
+    ap.add_argument("--cpu-roots", type=int, default=1)
+    ap.add_argument("--no-extras", action="store_true", help="skip plain/e2e/roofline passes")
+    ap.add_argument("--trace-out", default="")
+    return ap.parse_args()
+
+
+def workload(a) -> dict:
+    n = 1 << a.scale
+    return {"workload": f"rmat_s{a.scale}_ef{a.edgefactor}_edge_tree_bfs", "scale": a.scale,
+            "edgefactor": a.edgefactor, "n": n, "m": a.edgefactor * n, "roots": a.roots, "mh": a.mh,
+            "initiator": [0.57, 0.19, 0.19, 0.05], "seed": a.seed, "root_seed": a.root_seed,
+            "l2": "inputs larger than L2 (graph and core CSR are GBs; 129 MB L2)",
+            "parallelism": "replicas"}
+
+
+def hmean(x):
+    x = [v for v in x if v > 0]
+    return len(x) / sum(1.0 / v for v in x) if x else 0.0
+
+
+# ---- CPU oracle leg (spawned process; never touches the GPU) -----------------------------
+
+def oracle_job(scale, edgefactor, seed, root_seed, nroots, warm, q):
+    """Builds the oracle graph (untimed), then times serial oracle BFS from nroots roots."""
+    try:
+        import graphgen
+        from oracle import OracleGraph, traversed_tuples
+        n = 1 << scale
+        t0 = time.time()
+        e = graphgen.rmat_edges(scale, edgefactor, seed=seed)
+        og = OracleGraph(e, n)
+        setup = time.time() - t0
+        roots = graphgen.pick_roots(root_seed, n, max(nroots, 1), og.degree())
+        res = []
+        for i in range(warm):
+            og.bfs(int(roots[i % len(roots)]))
+        for r in roots[:nroots].tolist():
+            t = time.perf_counter()
+            lv, _ = og.bfs(int(r))
+            dt = time.perf_counter() - t
+            res.append((int(r), dt, traversed_tuples(e, lv)))
+        q.put({"ok": True, "setup_s": setup, "runs": res})
+    except Exception as ex:  # reported in the JSON line, never fatal
+        q.put({"ok": False, "error": repr(ex)})
+
+
+def start_oracle(a, nroots, warm):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    p = ctx.Process(target=oracle_job, args=(a.scale, a.edgefactor, a.seed, a.root_seed, nroots, warm, q),
+                    daemon=True)
+    p.start()
+    return p, q
+
+
+def oracle_result(p, q, timeout):
+    try:
+        r = q.get(timeout=timeout)
+    except Exception:
+        r = {"ok": False, "error": "oracle leg timed out"}
+    if p.is_alive():
+        p.kill()
+    return r
+
+
+def cpu_baseline_obj(r, nroots):
+    if not r.get("ok"):
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": r.get("error")}
+    gteps = [m / dt / 1e9 for (_, dt, m) in r["runs"]]
+    return {"value": hmean(gteps), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"serial oracle BFS (Alg. 1 top-down, min-id parents) from the first {nroots} of the "
+                      f"same seeded roots on the same scale-26 graph; oracle graph built untimed "
+                      f"({r['setup_s']:.0f} s with all host threads)",
+            "seconds": [round(dt, 3) for (_, dt, _) in r["runs"]]}
+
+
+# ---- clocks -------------------------------------------------------------------------------
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_index: int):
+        self.path = tempfile.mktemp(prefix="gt_clocks_", suffix=".csv")
+        self.dev = dev_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.send_signal(signal.SIGTERM)
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        rows = []
+        for ln in open(self.path):
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = sorted(v for v in (num(r[1]) for r in rows) if v is not None)
+        mx = max((v for v in (num(r[2]) for r in rows) if v is not None), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---- roofline helpers ---------------------------------------------------------------------
+
+def bu_bytes(lv: dict, n_core: int, visited_before: int, nwords: int) -> float:
+    """Algorithmic bytes of one bottom-up step: read + write the visited bitmap, one int64
+    row offset per unvisited vertex, 4 B per adjacency entry examined plus its 1-bit
+    visited probe, and 12 B (state + queue) per vertex found."""
+    unvisited = n_core - visited_before
+    return 8.0 * nwords + 8.0 * unvisited + 4.125 * lv["examined"] + 12.0 * lv["discovered"]
+
+
+def td_bytes(lv: dict) -> float:
+    """Top-down step: 16 B of row offsets per frontier vertex, 4 B per frontier edge plus its
+    1-bit visited probe, 28 B per vertex found (8 B state, 4 B queue, 16 B of its offsets)."""
+    return 16.0 * lv["frontier"] + 4.125 * lv["frontier_edges"] + 28.0 * lv["discovered"]
+
+
+def traffic_from_profiles(kernel: str) -> float | None:
+    """ncu DRAM bytes per launch recorded under profiles/, if taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    h = re.search(r"source_sha256:\s*([0-9a-f]+)", txt)
+    b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    src = open(os.path.join(ROOT, "paper_2009_07463_gb300", "csrc", "bfs.cu"), "rb").read()
+    if not h or not b or h.group(1) != hashlib.sha256(src).hexdigest()[:16]:
+        return None
+    return float(b.group(1))
+
+
+def launches_of(trace: list[dict]) -> int:
+    """Kernels one gt_bfs launches: reset, start, per level select + step kernels + decide,
+    output and the root-walk fix-up (resolve passes are absent at MH = 0 but for K2 tops)."""
+    k = 4
+    if not trace:
+        return k + 4
+    prev = None
+    for t in trace:
+        k += 2  # select, decide
+        if t["direction"] == "td":
+            k += 2
+        else:
+            k += 2 if prev == "td" else 1
+        prev = t["direction"]
+    return k
+
+
+# ---- main ---------------------------------------------------------------------------------
+
+def main():
+    a = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        return run_reference(a, world, rank)
+
+    # the oracle leg is spawned before the first GPU call
+    oracle = None
+    if a.cpu_baseline == "on" and rank == 0 and world == 1:
+        oracle = start_oracle(a, a.cpu_roots, 0)
+
+    import numpy as np
+    import torch
+
+    import graphgen
+    import paper_2009_07463_gb300 as gt
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    n = 1 << a.scale
+    m = a.edgefactor * n
+    cfg = workload(a)
+
+    # graph: device-resident tuples, built once (untimed)
+    edges = torch.empty((m, 2), dtype=torch.int64, device=dev)
+    graphgen.rmat_edges_device(edges.data_ptr(), a.scale, m, seed=a.seed, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    g = gt.gt_graph_build(edges, n, mh=a.mh, stream=stream)
+    torch.cuda.synchronize()
+    build_s = time.time() - t0
+    st = g.stats()
+    deg = g.degree()
+    all_roots = graphgen.pick_roots(a.root_seed, n, a.roots * world, deg)
+    roots = all_roots[rank * a.roots:(rank + 1) * a.roots].tolist()
+
+    parent = torch.empty(n, dtype=torch.int32, device=dev)
+    level = torch.empty(n, dtype=torch.int32, device=dev)
+
+    # per-root TEPS numerator and level trace (untimed)
+    tuples, traces = [], []
+    for r in roots:
+        g.bfs(r, parent, level, stream=stream)
+        traces.append(g.trace())
+        tuples.append(gt.gt_count_traversed(edges, level, stream=stream))
+
+    def one_step(fn, record):
+        evs = []
+        for r in roots:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(r, parent, level, stream=stream)
+            e1.record(stream)
+            evs.append((e0, e1))
+        if record is not None:
+            record.append(evs)
+
+    for _ in range(a.warmup):
+        one_step(g.bfs, None)
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    tstart = torch.cuda.Event(enable_timing=True)
+    tend = torch.cuda.Event(enable_timing=True)
+    rec = []
+    tstart.record(stream)
+    for _ in range(a.steps):
+        one_step(g.bfs, rec)
+    tend.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = tstart.elapsed_time(tend)
+    run_ms = [[e0.elapsed_time(e1) for (e0, e1) in step] for step in rec]
+    gteps = [tuples[i] / (ms * 1e-3) / 1e9 for step in run_ms for i, ms in enumerate(step)]
+    hm = hmean(gteps)
+    am = sum(gteps) / len(gteps)
+    ms_per_step = total_ms / a.steps
+    if dist:
+        t = torch.tensor([ms_per_step, hm], dtype=torch.float64, device=dev)
+        gathered = [torch.zeros_like(t) for _ in range(world)]
+        dist.all_gather(gathered, t)
+        ms_per_step = max(float(x[0]) for x in gathered)
+        hm_all = hmean([float(x[1]) for x in gathered])
+        value = world * hm_all
+    else:
+        value = hm
+    launches_per_step = sum(launches_of(tr) for tr in traces)
+
+    out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic", "config": cfg,
+           "gpu_launches": launches_per_step * a.steps, "clocks": clk,
+           "gteps_arith_mean": round(am, 3),
+           "graph": {"nnz": st["nnz"], "n_core": st["n_core"], "nnz_core": st["nnz_core"],
+                     "classes_CI_CE_TI_TL_VZ": st["n_class"], "build_s": round(build_s, 2),
+                     "device_gb": round(st["device_bytes"] / 1e9, 2)}}
+
+    if not a.no_extras:
+        # (a) plain direction-optimizing BFS on the unsplit graph, same roots, same timing
+        for _ in range(1):
+            one_step(g.bfs_plain, None)
+        prec = []
+        one_step(g.bfs_plain, prec)
+        torch.cuda.synchronize()
+        pg = [tuples[i] / (e0.elapsed_time(e1) * 1e-3) / 1e9 for i, (e0, e1) in enumerate(prec[0])]
+        out["plain_do_bfs"] = {"value": round(hmean(pg), 3), "unit": UNIT,
+                               "et_over_plain": round(hm / hmean(pg), 3) if hmean(pg) else None}
+
+        # end to end through the C-ABI: host (pinned) output buffers, copies inside the timing
+        hp = torch.empty(n, dtype=torch.int32).pin_memory()
+        hl = torch.empty(n, dtype=torch.int32).pin_memory()
+        g.bfs(roots[0], hp, hl, stream=stream)
+        eg = []
+        for i, r in enumerate(roots):
+            t = time.perf_counter()
+            g.bfs(r, hp, hl, stream=stream)  # returns once the results are in host memory
+            eg.append(tuples[i] / (time.perf_counter() - t) / 1e9)
+        out["e2e"] = {"value": round(hmean(eg), 3), "unit": UNIT, "h2d_bytes_per_step": 8 * len(roots),
+                      "d2h_bytes_per_step": 8 * n * len(roots),
+                      "how": "gt_bfs with pinned host parent/level buffers; D2H copy and stream sync inside each "
+                             "timed call; root passed by value"}
+
+        # roofline of the bottom-up kernel: work counts, then CUDA-event durations per launch
+        g.set_tuning(count_work=1, launch_mode=1)
+        counted = []
+        for r in roots:
+            g.bfs(r, parent, level, stream=stream)
+            counted.append(g.trace())
+        g.set_tuning(count_work=0, launch_mode=1, time_kernels=1)
+        timed = []
+        for r in roots:
+            g.bfs(r, parent, level, stream=stream)
+            timed.append(g.trace())
+        g.set_tuning(count_work=0, launch_mode=0, time_kernels=0)
+        nc = st["n_core"]
+        nwords = -(-max(nc, 1) // 32)
+        nwords = -(-nwords // 128) * 128
+        bu_b = bu_t = td_b = td_t = 0.0
+        bu_n = td_n = 0
+        for cw, tm in zip(counted, timed):
+            visited = 1
+            for lc, lt in zip(cw, tm):
+                if lc["direction"] == "bu":
+                    bu_b += bu_bytes(lc, nc, visited, nwords)
+                    bu_t += lt["step_ms"]
+                    bu_n += 1
+                else:
+                    td_b += td_bytes(lc)
+                    td_t += lt["step_ms"]
+                    td_n += 1
+                visited += lc["discovered"]
+        import json as _j
+        peaks = _j.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+        peak = peaks.get("hbm_gbs", 6800.0)
+        peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+        bu_gbs = bu_b / (bu_t * 1e-3) / 1e9 if bu_t > 0 else 0.0
+        td_gbs = td_b / (td_t * 1e-3) / 1e9 if td_t > 0 else 0.0
+        trf = traffic_from_profiles("bfs_bu")
+        out["roofline"] = {"bound": "hbm", "kernel": "bfs_bu", "achieved": round(bu_gbs, 1), "peak": peak,
+                           "peak_source": peak_src, "unit": "GB/s", "frac": round(bu_gbs / peak, 4),
+                           "traffic": trf, "launches": bu_n,
+                           "bytes_per_launch": round(bu_b / max(bu_n, 1)),
+                           "ms_per_launch": round(bu_t / max(bu_n, 1), 4),
+                           "share_of_step_time": round(bu_t / (bu_t + td_t), 3) if bu_t + td_t > 0 else None,
+                           "td": {"achieved": round(td_gbs, 1), "frac": round(td_gbs / peak, 4), "launches": td_n,
+                                  "ms_per_launch": round(td_t / max(td_n, 1), 4)},
+                           "how": "achieved = algorithmic bytes from per-level work counts / kernel duration from "
+                                  "CUDA events around each launch (host-driven kernel-timing pass, same roots)"}
+        if a.trace_out:
+            json.dump({"roots": roots, "counted": counted, "timed": timed, "tuples": tuples,
+                       "run_ms": run_ms}, open(a.trace_out, "w"))
+
+    if oracle is not None:
+        out["cpu_baseline"] = cpu_baseline_obj(oracle_result(*oracle, timeout=1800), a.cpu_roots)
+        if out["cpu_baseline"]["value"]:
+            out["cpu_baseline"]["cores"] = 1
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_reference(a, world, rank):
+    """The CPU oracle timed as the reference arm: W + K steps, one seeded root per step."""
+    if rank != 0:
+        return
+    import graphgen
+    from oracle import OracleGraph, traversed_tuples
+    n = 1 << a.scale
+    t0 = time.time()
+    e = graphgen.rmat_edges(a.scale, a.edgefactor, seed=a.seed)
+    og = OracleGraph(e, n)
+    setup = time.time() - t0
+    roots = graphgen.pick_roots(a.root_seed, n, a.roots, og.degree()).tolist()
+    for i in range(a.warmup):
+        og.bfs(roots[i % len(roots)])
+    runs = []
+    tt = time.perf_counter()
+    for i in range(a.steps):
+        r = roots[i % len(roots)]
+        t = time.perf_counter()
+        lv, _ = og.bfs(r)
+        dt = time.perf_counter() - t
+        runs.append(traversed_tuples(e, lv) / dt / 1e9)
+    total = time.perf_counter() - tt
+    v = hmean(runs)
+    out = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": UNIT, "n_gpus": world,
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(1e3 * total / a.steps, 1),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+           "data": "synthetic", "config": workload(a),
+           "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"one seeded root per step on the same scale-{a.scale} graph; serial oracle "
+                                      f"BFS; oracle graph built untimed in {setup:.0f} s"},
+           "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

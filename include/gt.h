@@ -72,6 +72,8 @@ typedef struct gt_tuning {
   int32_t launch_mode;  /* 0 = whole level loop in one CUDA graph with device-side
                            control (default), 1 = host-driven loop (one readback per level) */
   int32_t count_work;   /* 1: count examined edges per level (slower; for the trace) */
+  int32_t time_kernels; /* 1 (with launch_mode = 1): time each level's step kernels with
+                           CUDA events on the caller's stream; reported in the trace */
 } gt_tuning;
 
 typedef struct gt_stats {
@@ -95,6 +97,7 @@ typedef struct gt_level_info {
   int64_t unvisited_edges; /* m_u before the step */
   int64_t discovered;   /* vertices found by the step */
   int64_t examined;     /* adjacency entries read by the step (count_work = 1), else -1 */
+  double step_ms;       /* duration of the step's kernels (time_kernels = 1), else -1 */
 } gt_level_info;
 
 typedef struct gt_graph* gt_graph_t;

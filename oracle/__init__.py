@@ -36,7 +36,7 @@ def build() -> str:
         os.makedirs(os.path.dirname(_SO), exist_ok=True)
         tmp = _SO + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-fvisibility=hidden",
-                               "-o", tmp, srcs[0]])
+                               "-pthread", "-o", tmp, srcs[0]])
         os.replace(tmp, _SO)
     return _SO
 
@@ -47,7 +47,7 @@ def _load():
         if _lib is None:
             lib = ctypes.CDLL(build())
             p, i64 = ctypes.c_void_p, ctypes.c_int64
-            lib.or_graph_build.argtypes = [p, i64, i64]
+            lib.or_graph_build.argtypes = [p, i64, i64, ctypes.c_int]
             lib.or_graph_build.restype = p
             lib.or_graph_free.argtypes = [p]
             lib.or_graph_free.restype = None
@@ -75,12 +75,13 @@ def _edges(edges) -> np.ndarray:
 class OracleGraph:
     """Simple undirected graph of an edge-tuple list, held by the C oracle."""
 
-    def __init__(self, edges, n: int):
+    def __init__(self, edges, n: int, threads: int | None = None):
         self._lib = _load()
         e = _edges(edges)
         self.n = int(n)
         self.m = int(e.shape[0])
-        h = self._lib.or_graph_build(e.ctypes.data, e.shape[0], self.n)
+        threads = threads or min(64, os.cpu_count() or 1)
+        h = self._lib.or_graph_build(e.ctypes.data, e.shape[0], self.n, int(threads))
         if not h:
             raise ValueError("oracle: vertex id out of range or out of memory")
         self._h = h

@@ -26,6 +26,7 @@
  */
 #include "oracle.h"
 
+#include <pthread.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -41,44 +42,88 @@ static int cmp_i32(const void* a, const void* b) {
   return (x > y) - (x < y);
 }
 
-or_graph* or_graph_build(const int64_t* edges, int64_t m, int64_t n) {
+/* Graph construction is not part of what the oracle times (only or_bfs is), so its
+ * three passes are split across `nthreads` POSIX threads. Each pass is order-independent:
+ * the fill order within a row is arbitrary and every row is sorted afterwards, so the
+ * result is the same for any thread count. */
+typedef struct build_job {
+  const int64_t* edges;
+  int64_t lo, hi; /* tuple range (count, fill) or vertex range (sort) */
+  int64_t* cnt;
+  int64_t* start;
+  int64_t* fill;
+  int32_t* adj;
+  int pass;
+} build_job;
+
+static void* build_worker(void* arg) {
+  build_job* j = (build_job*)arg;
+  if (j->pass == 0) { /* degree counts with duplicates, self-loops skipped */
+    for (int64_t i = j->lo; i < j->hi; ++i) {
+      int64_t u = j->edges[2 * i], v = j->edges[2 * i + 1];
+      if (u == v) continue;
+      __atomic_fetch_add(&j->cnt[u], 1, __ATOMIC_RELAXED);
+      __atomic_fetch_add(&j->cnt[v], 1, __ATOMIC_RELAXED);
+    }
+  } else if (j->pass == 1) { /* bucket the directed entries by source */
+    for (int64_t i = j->lo; i < j->hi; ++i) {
+      int64_t u = j->edges[2 * i], v = j->edges[2 * i + 1];
+      if (u == v) continue;
+      j->adj[j->start[u] + __atomic_fetch_add(&j->fill[u], 1, __ATOMIC_RELAXED)] = (int32_t)v;
+      j->adj[j->start[v] + __atomic_fetch_add(&j->fill[v], 1, __ATOMIC_RELAXED)] = (int32_t)u;
+    }
+  } else { /* each row: sort ascending, keep one copy of each neighbour */
+    for (int64_t v = j->lo; v < j->hi; ++v) {
+      int32_t* a = j->adj + j->start[v];
+      int64_t k = j->start[v + 1] - j->start[v], w = 0;
+      qsort(a, (size_t)k, sizeof(int32_t), cmp_i32);
+      for (int64_t t = 0; t < k; ++t)
+        if (t == 0 || a[t] != a[t - 1]) a[w++] = a[t];
+      j->cnt[v] = w; /* deduplicated degree */
+    }
+  }
+  return NULL;
+}
+
+static void run_pass(build_job* proto, int pass, int64_t total, int nthreads) {
+  pthread_t tid[64];
+  build_job jobs[64];
+  if (nthreads < 1) nthreads = 1;
+  if (nthreads > 64) nthreads = 64;
+  int64_t chunk = (total + nthreads - 1) / nthreads;
+  for (int t = 0; t < nthreads; ++t) {
+    jobs[t] = *proto;
+    jobs[t].pass = pass;
+    jobs[t].lo = t * chunk < total ? t * chunk : total;
+    jobs[t].hi = (t + 1) * chunk < total ? (t + 1) * chunk : total;
+    if (nthreads == 1 || pthread_create(&tid[t], NULL, build_worker, &jobs[t]) != 0) {
+      build_worker(&jobs[t]);
+      tid[t] = 0;
+    }
+  }
+  for (int t = 0; t < nthreads; ++t)
+    if (nthreads > 1 && tid[t]) pthread_join(tid[t], NULL);
+}
+
+or_graph* or_graph_build(const int64_t* edges, int64_t m, int64_t n, int nthreads) {
   if (n < 0 || n > 2147483647LL || m < 0) return NULL;
   for (int64_t i = 0; i < 2 * m; ++i)
     if (edges[i] < 0 || edges[i] >= n) return NULL;
 
-  /* Directed entries (u,v) and (v,u) of every tuple with u != v, bucketed by source. */
   int64_t* cnt = calloc((size_t)n + 1, sizeof(int64_t));
-  if (!cnt) return NULL;
-  for (int64_t i = 0; i < m; ++i) {
-    int64_t u = edges[2 * i], v = edges[2 * i + 1];
-    if (u == v) continue;
-    cnt[u]++;
-    cnt[v]++;
-  }
   int64_t* start = malloc(((size_t)n + 1) * sizeof(int64_t));
-  if (!start) { free(cnt); return NULL; }
+  int64_t* fill = calloc((size_t)n + 1, sizeof(int64_t));
+  if (!cnt || !start || !fill) { free(cnt); free(start); free(fill); return NULL; }
+  build_job job = {edges, 0, 0, cnt, start, fill, NULL, 0};
+  run_pass(&job, 0, m, nthreads);
   start[0] = 0;
   for (int64_t v = 0; v < n; ++v) start[v + 1] = start[v] + cnt[v];
   int32_t* adj = malloc((size_t)(start[n] > 0 ? start[n] : 1) * sizeof(int32_t));
-  int64_t* fill = calloc((size_t)n + 1, sizeof(int64_t));
-  if (!adj || !fill) { free(cnt); free(start); free(adj); free(fill); return NULL; }
-  for (int64_t i = 0; i < m; ++i) {
-    int64_t u = edges[2 * i], v = edges[2 * i + 1];
-    if (u == v) continue;
-    adj[start[u] + fill[u]++] = (int32_t)v;
-    adj[start[v] + fill[v]++] = (int32_t)u;
-  }
-
-  /* Each adjacency list: sort ascending, keep one copy of each neighbour. */
-  int64_t* deg = cnt; /* reuse */
-  for (int64_t v = 0; v < n; ++v) {
-    int32_t* a = adj + start[v];
-    int64_t k = start[v + 1] - start[v], w = 0;
-    qsort(a, (size_t)k, sizeof(int32_t), cmp_i32);
-    for (int64_t j = 0; j < k; ++j)
-      if (j == 0 || a[j] != a[j - 1]) a[w++] = a[j];
-    deg[v] = w;
-  }
+  if (!adj) { free(cnt); free(start); free(fill); return NULL; }
+  job.adj = adj;
+  run_pass(&job, 1, m, nthreads);
+  run_pass(&job, 2, n, nthreads);
+  int64_t* deg = cnt;
 
   or_graph* g = malloc(sizeof(or_graph));
   if (!g) { free(cnt); free(start); free(adj); free(fill); return NULL; }

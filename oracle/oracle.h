@@ -20,9 +20,10 @@ enum {
 
 typedef struct or_graph or_graph;
 
-/* Simple undirected graph of m tuples edges[2i], edges[2i+1] over [0, n). NULL on a
- * vertex id outside [0, n) or on allocation failure. */
-OR_EXPORT or_graph* or_graph_build(const int64_t* edges, int64_t m, int64_t n);
+/* Simple undirected graph of m tuples edges[2i], edges[2i+1] over [0, n), built with
+ * nthreads threads (same result for any count). NULL on a vertex id outside [0, n) or on
+ * allocation failure. */
+OR_EXPORT or_graph* or_graph_build(const int64_t* edges, int64_t m, int64_t n, int nthreads);
 OR_EXPORT void or_graph_free(or_graph* g);
 OR_EXPORT int64_t or_graph_n(const or_graph* g);
 OR_EXPORT int64_t or_graph_nnz(const or_graph* g);

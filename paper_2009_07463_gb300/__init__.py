@@ -26,7 +26,7 @@ class gt_config(ctypes.Structure):
 class gt_tuning(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
         "alpha", "beta", "td_warp_min", "td_grid_min", "bu_thread_scan", "blocks_per_sm",
-        "force_direction", "launch_mode", "count_work")]
+        "force_direction", "launch_mode", "count_work", "time_kernels")]
 
 
 class gt_stats(ctypes.Structure):
@@ -38,7 +38,7 @@ class gt_stats(ctypes.Structure):
 class gt_level_info(ctypes.Structure):
     _fields_ = [("level", ctypes.c_int32), ("direction", ctypes.c_int32), ("frontier", ctypes.c_int64),
                 ("frontier_edges", ctypes.c_int64), ("unvisited_edges", ctypes.c_int64),
-                ("discovered", ctypes.c_int64), ("examined", ctypes.c_int64)]
+                ("discovered", ctypes.c_int64), ("examined", ctypes.c_int64), ("step_ms", ctypes.c_double)]
 
 
 class GtError(RuntimeError):
@@ -200,7 +200,7 @@ class Graph:
             t = arr[i]
             out.append({"level": t.level, "direction": "bu" if t.direction else "td", "frontier": t.frontier,
                         "frontier_edges": t.frontier_edges, "unvisited_edges": t.unvisited_edges,
-                        "discovered": t.discovered, "examined": t.examined})
+                        "discovered": t.discovered, "examined": t.examined, "step_ms": t.step_ms})
         return out
 
 

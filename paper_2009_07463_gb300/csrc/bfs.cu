@@ -365,6 +365,7 @@ __global__ void bfs_decide(BfsArgs a, cudaGraphConditionalHandle h_loop, int use
       t.unvisited_edges = c->m_u;
       t.discovered = nn;
       t.examined = a.count_work ? c->examined : -1;
+      t.step_ms = -1.0;
     }
     c->nlevels += 1;
     c->m_u -= nm;
@@ -661,6 +662,7 @@ int build_loop_graph(gt_graph* g, const View& v, cudaGraphExec_t* out) {
 
 int run_level_loop(gt_graph* g, View& v, int which, cudaStream_t s) {
   const gt_tuning& t = g->tuning;
+  g->step_ms.clear();
   if (t.launch_mode == 0) {
     if (!g->loop_exec[which]) {
       int rc = build_loop_graph(g, v, &g->loop_exec[which]);
@@ -675,11 +677,23 @@ int run_level_loop(gt_graph* g, View& v, int which, cudaStream_t s) {
     int32_t level, dir, done, cur, vcur, need_mark;
   } h{};
   const cudaGraphConditionalHandle none = 0;
+  int timed_steps = 0;
+  g->step_ms.clear();
   for (int guard = 0; guard < (1 << 30); ++guard) {
     int rc = cuda_fail(cudaMemcpyAsync(&h, v.ctl, sizeof(h), cudaMemcpyDeviceToHost, s), "ctl readback");
     if (rc == GT_OK) rc = cuda_fail(cudaStreamSynchronize(s), "level sync");
     if (rc != GT_OK) return rc;
     if (h.done) break;
+    const bool timed = t.time_kernels && guard < MAX_TRACE;
+    if (timed) {
+      while ((int)g->step_events.size() < 2 * (guard + 1)) {
+        cudaEvent_t ev;
+        rc = cuda_fail(cudaEventCreate(&ev), "event create");
+        if (rc != GT_OK) return rc;
+        g->step_events.push_back(ev);
+      }
+      cudaEventRecord(g->step_events[2 * guard], s);
+    }
     if (h.dir == DIR_TD) {
       bfs_td<<<grid, BFS_THREADS, 0, s>>>(a);
       bfs_td_grid<<<grid, BFS_THREADS, 0, s>>>(a);
@@ -687,9 +701,21 @@ int run_level_loop(gt_graph* g, View& v, int which, cudaStream_t s) {
       if (h.need_mark) bfs_mark<<<grid, BFS_THREADS, 0, s>>>(a);
       bfs_bu<<<grid, BFS_THREADS, 0, s>>>(a);
     }
+    if (timed) {
+      cudaEventRecord(g->step_events[2 * guard + 1], s);
+      ++timed_steps;
+    }
     bfs_decide<<<1, 1, 0, s>>>(a, none, 0);
     rc = cuda_fail(cudaGetLastError(), "level launch");
     if (rc != GT_OK) return rc;
+  }
+  for (int i = 0; i < timed_steps; ++i) {
+    float ms = -1.f;
+    if (cudaEventElapsedTime(&ms, g->step_events[2 * i], g->step_events[2 * i + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      ms = -1.f;
+    }
+    g->step_ms.push_back(ms);
   }
   return GT_OK;
 }

@@ -365,6 +365,8 @@ static void free_view(View& v) {
 void free_graph(gt_graph* g) {
   for (int i = 0; i < 2; ++i)
     if (g->loop_exec[i]) cudaGraphExecDestroy(g->loop_exec[i]);
+  for (cudaEvent_t ev : g->step_events) cudaEventDestroy(ev);
+  g->step_events.clear();
   if (g->core.row != g->row) {
     cudaFree(g->core.row);
     cudaFree(g->core.col);

@@ -139,6 +139,7 @@ GT_API void gt_tuning_default(gt_tuning* t) {
   t->force_direction = 0;
   t->launch_mode = 0;
   t->count_work = 0;
+  t->time_kernels = 0;
 }
 
 GT_API int gt_graph_build(const int64_t* edges, int64_t m, int64_t n, const gt_config* cfg, void* stream,
@@ -217,7 +218,8 @@ GT_API int gt_graph_set_tuning(gt_graph_t g, const gt_tuning* t) {
   if (!g || !t) return GT_EINVAL;
   if (t->alpha < 1 || t->beta < 1 || t->td_warp_min < 1 || t->td_grid_min < t->td_warp_min ||
       t->bu_thread_scan < 0 || t->blocks_per_sm < 1 || t->blocks_per_sm > 32 || t->force_direction < 0 ||
-      t->force_direction > 2 || t->launch_mode < 0 || t->launch_mode > 1) {
+      t->force_direction > 2 || t->launch_mode < 0 || t->launch_mode > 1 || t->time_kernels < 0 ||
+      t->time_kernels > 1 || (t->time_kernels && t->launch_mode != 1)) {
     set_error("gt_graph_set_tuning: value out of range");
     return GT_EINVAL;
   }
@@ -255,6 +257,7 @@ GT_API int gt_bfs_trace(gt_graph_t g, gt_level_info* out, int32_t cap, int32_t* 
   if (k > MAX_TRACE) k = MAX_TRACE;
   if (k > 0)
     rc = cuda_fail(cudaMemcpy(out, g->last_ctl->trace, sizeof(gt_level_info) * k, cudaMemcpyDeviceToHost), "trace");
+  for (int32_t i = 0; i < k && i < (int32_t)g->step_ms.size(); ++i) out[i].step_ms = g->step_ms[i];
   return rc;
 }
 

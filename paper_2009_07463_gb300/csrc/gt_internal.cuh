@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "gt.h"
 
@@ -95,6 +96,9 @@ struct gt_graph {
   gt::BfsCtl* last_ctl = nullptr;
   // CUDA graphs of the level loop, one per view, instantiated lazily
   cudaGraphExec_t loop_exec[2] = {nullptr, nullptr};
+  // step timing (time_kernels): one event pair per level, host copy of the durations
+  std::vector<cudaEvent_t> step_events;
+  std::vector<double> step_ms;
   int64_t device_bytes = 0;
 };
 
