@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--cpu-roots", type=int, default=1)
     ap.add_argument("--no-extras", action="store_true", help="skip plain/e2e/roofline passes")
     ap.add_argument("--trace-out", default="")
+    ap.add_argument("--launch-mode", default="graph", choices=["graph", "host"],
+                    help="host: one launch per kernel (lets ncu see every kernel; slower)")
     return ap.parse_args()
 
 
@@ -213,17 +215,18 @@ def traffic_from_profiles(kernel: str) -> float | None:
 
 def launches_of(trace: list[dict]) -> int:
     """Kernels one gt_bfs launches: reset, start, per level select + step kernels + decide,
-    output and the root-walk fix-up (resolve passes are absent at MH = 0 but for K2 tops)."""
+    output and the root-walk fix-up (resolve passes are absent at MH = 0 but for K2 tops).
+    Step kernels: top-down 1; bottom-up 2 (gather, scan), plus a mark after a top-down step."""
     k = 4
     if not trace:
-        return k + 4
+        return k + 3
     prev = None
     for t in trace:
         k += 2  # select, decide
         if t["direction"] == "td":
-            k += 2
+            k += 1
         else:
-            k += 2 if prev == "td" else 1
+            k += 3 if prev == "td" else 2
         prev = t["direction"]
     return k
 
@@ -268,6 +271,8 @@ def main():
     g = gt.gt_graph_build(edges, n, mh=a.mh, stream=stream)
     torch.cuda.synchronize()
     build_s = time.time() - t0
+    if a.launch_mode == "host":
+        g.set_tuning(launch_mode=1)
     st = g.stats()
     deg = g.degree()
     all_roots = graphgen.pick_roots(a.root_seed, n, a.roots * world, deg)
@@ -377,7 +382,7 @@ def main():
         for r in roots:
             g.bfs(r, parent, level, stream=stream)
             timed.append(g.trace())
-        g.set_tuning(count_work=0, launch_mode=0, time_kernels=0)
+        g.set_tuning(count_work=0, launch_mode=1 if a.launch_mode == "host" else 0, time_kernels=0)
         nc = st["n_core"]
         nwords = -(-max(nc, 1) // 32)
         nwords = -(-nwords // 128) * 128
@@ -403,7 +408,7 @@ def main():
         bu_gbs = bu_b / (bu_t * 1e-3) / 1e9 if bu_t > 0 else 0.0
         td_gbs = td_b / (td_t * 1e-3) / 1e9 if td_t > 0 else 0.0
         trf = traffic_from_profiles("bfs_bu")
-        out["roofline"] = {"bound": "hbm", "kernel": "bfs_bu", "achieved": round(bu_gbs, 1), "peak": peak,
+        out["roofline"] = {"bound": "hbm", "kernel": "bfs_bu_gather+bfs_bu_scan", "achieved": round(bu_gbs, 1), "peak": peak,
                            "peak_source": peak_src, "unit": "GB/s", "frac": round(bu_gbs / peak, 4),
                            "traffic": trf, "launches": bu_n,
                            "bytes_per_launch": round(bu_b / max(bu_n, 1)),

@@ -64,16 +64,22 @@ typedef struct gt_tuning {
   int32_t alpha;        /* top-down -> bottom-up when m_f * alpha > m_u (default 14) */
   int32_t beta;         /* bottom-up -> top-down when n_f * beta < n and shrinking (24) */
   int32_t td_warp_min;  /* top-down: degree above which a whole warp takes a vertex (32) */
-  int32_t td_grid_min;  /* top-down: degree above which all CTAs share a vertex (4096) */
+  int32_t td_cta_min;   /* top-down: degree above which a whole CTA takes a vertex (256) */
+  int32_t td_grid_min;  /* top-down: degree above which the vertex's edges join one flat
+                           edge space shared by the whole grid (2048) */
   int32_t bu_thread_scan; /* bottom-up: neighbours a lane checks alone before the warp
                              takes the vertex over (8) */
-  int32_t blocks_per_sm;  /* CTAs per SM of the traversal kernels (4) */
+  int32_t blocks_per_sm;  /* CTAs per SM of the traversal kernels (8) */
   int32_t force_direction; /* 0 = switch heuristic, 1 = top-down only, 2 = bottom-up only */
   int32_t launch_mode;  /* 0 = whole level loop in one CUDA graph with device-side
                            control (default), 1 = host-driven loop (one readback per level) */
   int32_t count_work;   /* 1: count examined edges per level (slower; for the trace) */
   int32_t time_kernels; /* 1 (with launch_mode = 1): time each level's step kernels with
                            CUDA events on the caller's stream; reported in the trace */
+  int32_t batch_alpha;  /* gt_bfs_batch: lane word goes bottom-up when the next frontier's
+                           summed degree * batch_alpha > core edges (default 14) */
+  int32_t batch_beta;   /* gt_bfs_batch: back to top-down when frontier * batch_beta < core
+                           vertices and shrinking (default 24) */
 } gt_tuning;
 
 typedef struct gt_stats {
@@ -133,6 +139,24 @@ GT_API int gt_bfs(gt_graph_t g, int64_t root, int32_t* parent, int32_t* level, v
 /* The same contract on the unsplit graph (plain direction-optimizing BFS, Alg. 1); the
  * comparison baseline. GT_ENOTSUP if the handle was built with keep_plain = 0. */
 GT_API int gt_bfs_plain(gt_graph_t g, int64_t root, int32_t* parent, int32_t* level, void* stream);
+/* Batched BFS (multi-source BFS over 64-root lane words; no counterpart in the paper,
+ * which runs one root at a time): for every graph i and each of its roots_per_graph[i]
+ * roots (taken in order from `roots`), writes the same level and parent arrays gt_bfs
+ * would, as rows of parent[i] / level[i]: device int32 [roots_per_graph[i]][n_i], row r
+ * for root r. Roots are packed 64 to a lane word; the words of all graphs advance level
+ * by level in one persistent cooperative launch that shares every adjacency read among
+ * the word's roots. Per-graph lane-word storage (about 350 bytes per core vertex per 64
+ * roots) is allocated on first use and kept in the handle. At most 16384 roots per call.
+ * All graphs must live on one device. Synchronises `stream`. GT_ETIMEOUT if a bounded
+ * grid-barrier wait ran out, GT_ENOTSUP if a traversal is deeper than 65533 levels. */
+GT_API int gt_bfs_batch(const gt_graph_t* graphs, int32_t ngraphs, const int64_t* roots,
+                        const int32_t* roots_per_graph, int32_t* const* parent, int32_t* const* level,
+                        void* stream);
+/* Autotuner: times edge-tree BFS from nsample seeded roots of degree >= 1 (and one batch
+ * of up to 64 of them) under settings of gt_tuning, walking one parameter at a time, and
+ * keeps the fastest in the handle (also copied to *best if non-null). Results do not
+ * depend on the setting. Synchronises `stream`; allocates temporary device buffers. */
+GT_API int gt_autotune(gt_graph_t g, int32_t nsample, uint64_t seed, gt_tuning* best, void* stream);
 /* Per-level trace of the last gt_bfs / gt_bfs_plain on g (synchronises the stream it
  * ran on). Writes up to cap entries, *nlevels = levels run. */
 GT_API int gt_bfs_trace(gt_graph_t g, gt_level_info* out, int32_t cap, int32_t* nlevels);

@@ -25,8 +25,8 @@ class gt_config(ctypes.Structure):
 
 class gt_tuning(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
-        "alpha", "beta", "td_warp_min", "td_grid_min", "bu_thread_scan", "blocks_per_sm",
-        "force_direction", "launch_mode", "count_work", "time_kernels")]
+        "alpha", "beta", "td_warp_min", "td_cta_min", "td_grid_min", "bu_thread_scan", "blocks_per_sm",
+        "force_direction", "launch_mode", "count_work", "time_kernels", "batch_alpha", "batch_beta")]
 
 
 class gt_stats(ctypes.Structure):
@@ -72,6 +72,8 @@ def lib():
                 "gt_bfs": (ctypes.c_int, [p, i64, p, p, p]),
                 "gt_bfs_plain": (ctypes.c_int, [p, i64, p, p, p]),
                 "gt_bfs_trace": (ctypes.c_int, [p, p, i32, p]),
+                "gt_bfs_batch": (ctypes.c_int, [p, i32, p, p, p, p, p]),
+                "gt_autotune": (ctypes.c_int, [p, i32, ctypes.c_uint64, p, p]),
                 "gt_count_traversed": (ctypes.c_int, [p, i64, p, i64, p, p]),
                 "gt_strerror": (ctypes.c_char_p, [ctypes.c_int]),
                 "gt_last_error": (ctypes.c_char_p, []),
@@ -190,6 +192,12 @@ class Graph:
     def bfs_plain(self, root: int, parent=None, level=None, stream=None):
         return self.bfs(root, parent, level, stream, plain=True)
 
+    def autotune(self, nsample: int = 8, seed: int = 1, stream=None) -> gt_tuning:
+        """Picks and keeps the fastest gt_tuning for this graph (results never change)."""
+        t = gt_tuning()
+        _check(lib().gt_autotune(self._h, int(nsample), int(seed), ctypes.byref(t), _stream(stream)), "gt_autotune")
+        return t
+
     def trace(self) -> list[dict]:
         cap = 4096
         arr = (gt_level_info * cap)()
@@ -247,8 +255,25 @@ def gt_bfs_plain(g: Graph, root: int, parent=None, level=None, stream=None):
     return g.bfs_plain(root, parent, level, stream)
 
 
+def gt_autotune(g: Graph, nsample: int = 8, seed: int = 1, stream=None) -> gt_tuning:
+    return g.autotune(nsample, seed, stream)
+
+
 def gt_bfs_trace(g: Graph) -> list[dict]:
     return g.trace()
+
+
+def gt_bfs_batch(graphs, roots_per_graph, parents, levels, stream=None) -> None:
+    """Batched BFS: graphs[i] with roots roots_per_graph[i] (a sequence of vertex ids);
+    parents[i] / levels[i] are device int32 buffers of len(roots) * n_i (row r = root r)."""
+    ng = len(graphs)
+    hs = (ctypes.c_void_p * ng)(*[g.handle for g in graphs])
+    counts = (ctypes.c_int32 * ng)(*[len(r) for r in roots_per_graph])
+    flat = [int(x) for r in roots_per_graph for x in r]
+    ra = (ctypes.c_int64 * max(1, len(flat)))(*flat)
+    pp = (ctypes.c_void_p * ng)(*[_ptr(x) for x in parents])
+    lp = (ctypes.c_void_p * ng)(*[_ptr(x) for x in levels])
+    _check(lib().gt_bfs_batch(hs, ng, ra, counts, pp, lp, _stream(stream)), "gt_bfs_batch")
 
 
 def gt_count_traversed(edges, level, stream=None, m: int | None = None) -> int:

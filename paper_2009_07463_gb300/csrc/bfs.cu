@@ -6,9 +6,9 @@
 // the start of the level does atomicMin(state, (L+1) << 32 | v); the smallest packed
 // value wins, i.e. level L+1 with the smallest frontier neighbour as parent, and the
 // one thread that replaced UNVISITED enqueues the vertex. Bottom-up (Alg. 1 BOTTOM-UP,
-// with the block search of Alg. 5): unvisited vertices are found by scanning the
-// visited bitmap in 128-bit words; each scans its ascending adjacency and stops at the
-// first visited neighbour (visited before this level means "in the frontier" for an
+// with the block search of Alg. 5): unvisited vertices are gathered from the visited
+// bitmap in 128-bit words; each scans its ascending adjacency and stops at the first
+// visited neighbour (visited before this level means "in the frontier" for an
 // unvisited vertex), which is the smallest one. Both directions therefore give the
 // same levels and min-id parents, whatever the switch does.
 #include <algorithm>
@@ -30,11 +30,11 @@ struct BfsArgs {
   uint64_t* state;
   uint32_t* vis0;
   uint32_t* vis1;
-  int32_t* q0;
-  int32_t* q1;
-  int32_t* big;
+  int32_t* queues;  // [2][NBINS][n]
+  int32_t* ulist;
   BfsCtl* ctl;
   int32_t td_warp_min;
+  int32_t td_cta_min;
   int32_t td_grid_min;
   int32_t bu_scan;
   int32_t count_work;
@@ -50,31 +50,43 @@ BfsArgs make_args(const View& v, const gt_tuning& t) {
   a.state = v.state;
   a.vis0 = v.vis[0];
   a.vis1 = v.vis[1];
-  a.q0 = v.queue[0];
-  a.q1 = v.queue[1];
-  a.big = v.big;
+  a.queues = v.queues;
+  a.ulist = v.ulist;
   a.ctl = v.ctl;
   a.td_warp_min = std::max(1, t.td_warp_min);
-  a.td_grid_min = std::max(a.td_warp_min, t.td_grid_min);
+  a.td_cta_min = std::max(a.td_warp_min, t.td_cta_min);
+  a.td_grid_min = std::max(a.td_cta_min, t.td_grid_min);
   a.bu_scan = std::max(0, t.bu_thread_scan);
   a.count_work = t.count_work;
   return a;
 }
 
-// Appends the lanes with `disc` set to the next queue; all 32 lanes must call.
-__device__ __forceinline__ void warp_enqueue(bool disc, int32_t w, int64_t wdeg, int32_t* __restrict__ nq,
-                                             BfsCtl* ctl) {
+__device__ __forceinline__ int32_t* queue_of(const BfsArgs& a, int set, int bin) {
+  return a.queues + ((int64_t)(set * NBINS + bin)) * (a.n > 0 ? a.n : 1);
+}
+
+__device__ __forceinline__ int bin_of(const BfsArgs& a, int64_t d) {
+  return d <= a.td_warp_min ? 0 : (d <= a.td_cta_min ? 1 : (d <= a.td_grid_min ? 2 : 3));
+}
+
+// Appends the lanes with `disc` set to frontier queue set `set`, each into the queue of
+// its degree bin, with one atomic per non-empty bin per warp. All 32 lanes must call.
+__device__ __forceinline__ void warp_enqueue(bool disc, int32_t w, int64_t wdeg, const BfsArgs& a, int set,
+                                             int64_t* bin_n) {
   const unsigned bal = __ballot_sync(FULL, disc);
   if (!bal) return;
-  const int lane = threadIdx.x & 31, leader = __ffs(bal) - 1;
-  const int64_t dsum = warp_sum<int64_t>(disc ? wdeg : 0);
-  unsigned long long base = 0;
-  if (lane == leader) {
-    base = atomicAdd((unsigned long long*)&ctl->next_n, (unsigned long long)__popc(bal));
-    atomicAdd((unsigned long long*)&ctl->next_m, (unsigned long long)dsum);
+  const int lane = threadIdx.x & 31;
+  const int b = disc ? bin_of(a, wdeg) : -1;
+#pragma unroll
+  for (int k = 0; k < NBINS; ++k) {
+    const unsigned mk = __ballot_sync(FULL, b == k);
+    if (!mk) continue;
+    const int leader = __ffs(mk) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd((unsigned long long*)&bin_n[k], (unsigned long long)__popc(mk));
+    base = __shfl_sync(FULL, base, leader);
+    if (b == k) queue_of(a, set, k)[base + __popc(mk & lanemask_lt())] = w;
   }
-  base = __shfl_sync(FULL, base, leader);
-  if (disc) nq[base + __popc(bal & lanemask_lt())] = w;
 }
 
 // One frontier edge (v -> w) of a top-down step; packed = (L+1) << 32 | v.
@@ -85,271 +97,413 @@ __device__ __forceinline__ bool td_visit(uint64_t* state, const uint32_t* vis, i
   return old == UNVISITED;
 }
 
-__device__ __forceinline__ void add_examined(const BfsArgs& a, int64_t x) {
-  if (!a.count_work) return;
-  x = warp_sum(x);
-  if ((threadIdx.x & 31) == 0 && x) atomicAdd((unsigned long long*)&a.ctl->examined, (unsigned long long)x);
+// Adds per-thread counts into the control block with one atomic per CTA and counter.
+// Every thread of the CTA must call.
+__device__ __forceinline__ void block_commit(const BfsArgs& a, int64_t n_found, int64_t m_found, int64_t examined) {
+  __shared__ int64_t red[3][WARPS];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  n_found = warp_sum(n_found);
+  m_found = warp_sum(m_found);
+  examined = warp_sum(examined);
+  if (lane == 0) {
+    red[0][w] = n_found;
+    red[1][w] = m_found;
+    red[2][w] = examined;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t x = 0, y = 0, z = 0;
+    for (int i = 0; i < WARPS; ++i) {
+      x += red[0][i];
+      y += red[1][i];
+      z += red[2][i];
+    }
+    if (x) atomicAdd((unsigned long long*)&a.ctl->next_n, (unsigned long long)x);
+    if (y) atomicAdd((unsigned long long*)&a.ctl->next_m, (unsigned long long)y);
+    if (z && a.count_work) atomicAdd((unsigned long long*)&a.ctl->examined, (unsigned long long)z);
+  }
 }
 
-// ---- top-down ----------------------------------------------------------------------
-// A warp takes 32 frontier vertices. Degree <= td_warp_min: their edges are packed
-// across the warp's lanes (lane-to-vertex by a search over the prefix sum of degrees).
-// Up to td_grid_min: the whole warp walks one vertex's adjacency. Above: the vertex is
-// handed to bfs_td_grid, where every CTA of the grid takes a slice of it.
-__global__ void __launch_bounds__(BFS_THREADS) bfs_td(BfsArgs a) {
-  BfsCtl* ctl = a.ctl;
-  const int cur = ctl->cur;
-  const int32_t* __restrict__ q = cur ? a.q1 : a.q0;
-  int32_t* __restrict__ nq = cur ? a.q0 : a.q1;
-  uint32_t* vis = ctl->vcur ? a.vis1 : a.vis0;
-  const int64_t nf = ctl->n_f;
-  const uint64_t hi = (uint64_t)(uint32_t)(ctl->level + 1) << 32;
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = gtid() >> 5, nw = gthreads() >> 5;
-  int64_t examined = 0;
-  for (int64_t base = gw * 32; base < nf; base += nw * 32) {
-    const int64_t i = base + lane;
-    int32_t v = -1;
-    int64_t rs = 0, re = 0;
-    if (i < nf) {
-      v = q[i];
-      rs = a.row[v];
-      re = a.row[v + 1];
-      atomicOr(&vis[v >> 5], 1u << (v & 31));
-    }
-    const int64_t d = re - rs;
-    const bool big = d > a.td_grid_min;
-    {
-      const unsigned bal = __ballot_sync(FULL, big);
-      if (bal) {
-        unsigned long long b0 = 0;
-        if (lane == __ffs(bal) - 1) b0 = atomicAdd((unsigned long long*)&ctl->big_n, (unsigned long long)__popc(bal));
-        b0 = __shfl_sync(FULL, b0, __ffs(bal) - 1);
-        if (big) a.big[b0 + __popc(bal & lanemask_lt())] = v;
+// Walks the adjacency entries [s, e) of frontier vertex v with `stride` lanes starting at
+// lane offset `first`; all lanes of the warp take part in every step.
+__device__ __forceinline__ void td_edges(const BfsArgs& a, uint32_t* vis, int nxt, int32_t v, uint64_t hi,
+                                         int64_t s, int64_t e, int64_t first, int64_t stride, int64_t& nf,
+                                         int64_t& mf) {
+  const uint64_t packed = hi | (uint32_t)v;
+  for (int64_t k0 = s + first; k0 < e; k0 += stride) {
+    const int64_t k = k0 + (threadIdx.x & 31);
+    bool disc = false;
+    int32_t w = 0;
+    int64_t wd = 0;
+    if (k < e) {
+      w = a.col[k];
+      disc = td_visit(a.state, vis, w, packed);
+      if (disc) {
+        wd = a.row[w + 1] - a.row[w];
+        ++nf;
+        mf += wd;
       }
     }
-    unsigned med = __ballot_sync(FULL, !big && d > a.td_warp_min);
-    while (med) {
-      const int src = __ffs(med) - 1;
-      med &= med - 1;
-      const int32_t vv = __shfl_sync(FULL, v, src);
-      const int64_t s = __shfl_sync(FULL, rs, src), e = __shfl_sync(FULL, re, src);
-      const uint64_t packed = hi | (uint32_t)vv;
-      for (int64_t k0 = s; k0 < e; k0 += 32) {
-        const int64_t k = k0 + lane;
+    warp_enqueue(disc, w, wd, a, nxt, a.ctl->next_bin_n);
+  }
+}
+
+constexpr int TD_WIN = 1024;  // bin-3 vertices whose edges one window flattens
+
+// ---- top-down ----------------------------------------------------------------------
+// One launch, four phases over the four degree bins of the frontier (no grid barrier
+// between them):
+//  bin 3 (degree > td_grid_min): the edges of all such vertices form one flat index space
+//    (per-CTA prefix sums of their degrees, in windows of TD_WIN vertices); every warp of
+//    the grid takes 32 consecutive edges at a time and finds their vertex by binary
+//    search, so a few hubs spread over the whole GPU;
+//  bin 2: a CTA per vertex;  bin 1: a warp per vertex;
+//  bin 0 (degree <= td_warp_min): a warp takes 32 vertices and its lanes share out their
+//    edges (lane-to-vertex by a search over the warp's prefix sum of degrees).
+__global__ void __launch_bounds__(BFS_THREADS) bfs_td(BfsArgs a) {
+  __shared__ int64_t s_pre[TD_WIN + 1];
+  __shared__ int64_t s_beg[TD_WIN];
+  __shared__ int32_t s_v[TD_WIN];
+  __shared__ int64_t s_wsum[WARPS];
+  BfsCtl* ctl = a.ctl;
+  const int cur = ctl->cur, nxt = cur ^ 1;
+  uint32_t* vis = ctl->vcur ? a.vis1 : a.vis0;
+  const uint64_t hi = (uint64_t)(uint32_t)(ctl->level + 1) << 32;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t gw = gtid() >> 5, nw = gthreads() >> 5;
+  int64_t nf = 0, mf = 0, examined = 0;
+  // bin 3: flattened edge space
+  {
+    const int32_t* q = queue_of(a, cur, 3);
+    const int64_t nb = ctl->bin_n[3];
+    for (int64_t ws = 0; ws < nb; ws += TD_WIN) {
+      const int cnt = (int)min((int64_t)TD_WIN, nb - ws);
+      // each thread owns 4 consecutive window slots; block scan of their degree sums
+      int64_t d4[4], loc = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int t = threadIdx.x * 4 + k;
+        d4[k] = 0;
+        if (t < cnt) {
+          const int32_t v = q[ws + t];
+          const int64_t b = a.row[v];
+          d4[k] = a.row[v + 1] - b;
+          s_v[t] = v;
+          s_beg[t] = b;
+          if (blockIdx.x == 0) atomicOr(&vis[v >> 5], 1u << (v & 31));
+        }
+        loc += d4[k];
+      }
+      const int64_t incl = warp_incl_scan(loc);
+      if (lane == 31) s_wsum[wib] = incl;
+      __syncthreads();
+      int64_t pre = incl - loc;
+      for (int i = 0; i < wib; ++i) pre += s_wsum[i];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int t = threadIdx.x * 4 + k;
+        if (t < cnt) s_pre[t] = pre;
+        pre += d4[k];
+      }
+      if (threadIdx.x == BFS_THREADS - 1) s_pre[cnt] = pre;
+      __syncthreads();
+      const int64_t E = s_pre[cnt];
+      if (blockIdx.x == 0 && threadIdx.x == 0) examined += E;
+      for (int64_t c0 = gw * 32; c0 < E; c0 += nw * 32) {
+        const int64_t off = c0 + lane;
         bool disc = false;
         int32_t w = 0;
         int64_t wd = 0;
-        if (k < e) {
-          w = a.col[k];
-          disc = td_visit(a.state, vis, w, packed);
-          if (disc) wd = a.row[w + 1] - a.row[w];
+        if (off < E) {
+          int lo = 0, hi2 = cnt - 1;  // largest idx with s_pre[idx] <= off
+          while (lo < hi2) {
+            const int mid = (lo + hi2 + 1) >> 1;
+            if (s_pre[mid] <= off) lo = mid; else hi2 = mid - 1;
+          }
+          const int32_t v = s_v[lo];
+          w = a.col[s_beg[lo] + (off - s_pre[lo])];
+          disc = td_visit(a.state, vis, w, hi | (uint32_t)v);
+          if (disc) {
+            wd = a.row[w + 1] - a.row[w];
+            ++nf;
+            mf += wd;
+          }
         }
-        warp_enqueue(disc, w, wd, nq, ctl);
+        warp_enqueue(disc, w, wd, a, nxt, ctl->next_bin_n);
       }
-      if (lane == 0) examined += e - s;
+      __syncthreads();
     }
-    const int32_t sd = (!big && d <= a.td_warp_min) ? (int32_t)d : 0;
-    const int32_t incl = warp_incl_scan(sd);
-    const int32_t total = __shfl_sync(FULL, incl, 31);
-    const int32_t excl = incl - sd;
-    if (lane == 0) examined += total;
-    for (int32_t r0 = 0; r0 < total; r0 += 32) {
-      const int32_t idx = r0 + lane;
-      int owner = 0;
+  }
+  // bin 2: a CTA per vertex
+  {
+    const int32_t* q = queue_of(a, cur, 2);
+    const int64_t nb = ctl->bin_n[2];
+    for (int64_t j = blockIdx.x; j < nb; j += gridDim.x) {
+      const int32_t v = q[j];
+      const int64_t s = a.row[v], e = a.row[v + 1];
+      if (threadIdx.x == 0) {
+        atomicOr(&vis[v >> 5], 1u << (v & 31));
+        examined += e - s;
+      }
+      td_edges(a, vis, nxt, v, hi, s, e, (int64_t)wib * 32, (int64_t)WARPS * 32, nf, mf);
+    }
+  }
+  // bin 1: a warp per vertex
+  {
+    const int32_t* q = queue_of(a, cur, 1);
+    const int64_t nb = ctl->bin_n[1];
+    for (int64_t j = gw; j < nb; j += nw) {
+      const int32_t v = q[j];
+      const int64_t s = a.row[v], e = a.row[v + 1];
+      if (lane == 0) {
+        atomicOr(&vis[v >> 5], 1u << (v & 31));
+        examined += e - s;
+      }
+      td_edges(a, vis, nxt, v, hi, s, e, 0, 32, nf, mf);
+    }
+  }
+  // bin 0: edges of 32 vertices packed across the warp's lanes
+  {
+    const int32_t* q = queue_of(a, cur, 0);
+    const int64_t nb = ctl->bin_n[0];
+    for (int64_t base = gw * 32; base < nb; base += nw * 32) {
+      const int64_t i = base + lane;
+      int32_t v = -1;
+      int64_t rs = 0, re = 0;
+      if (i < nb) {
+        v = q[i];
+        rs = a.row[v];
+        re = a.row[v + 1];
+        atomicOr(&vis[v >> 5], 1u << (v & 31));
+      }
+      const int32_t sd = (int32_t)(re - rs);
+      const int32_t incl = warp_incl_scan(sd);
+      const int32_t total = __shfl_sync(FULL, incl, 31);
+      const int32_t excl = incl - sd;
+      if (lane == 0) examined += total;
+      for (int32_t r0 = 0; r0 < total; r0 += 32) {
+        const int32_t idx = r0 + lane;
+        int owner = 0;
 #pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const int cand = owner + step;
-        if (__shfl_sync(FULL, excl, cand) <= idx) owner = cand;
+        for (int step = 16; step > 0; step >>= 1) {
+          const int cand = owner + step;
+          if (__shfl_sync(FULL, excl, cand) <= idx) owner = cand;
+        }
+        const int32_t ov = __shfl_sync(FULL, v, owner);
+        const int64_t ors = __shfl_sync(FULL, rs, owner);
+        const int32_t oex = __shfl_sync(FULL, excl, owner);
+        bool disc = false;
+        int32_t w = 0;
+        int64_t wd = 0;
+        if (idx < total) {
+          w = a.col[ors + (idx - oex)];
+          disc = td_visit(a.state, vis, w, hi | (uint32_t)ov);
+          if (disc) {
+            wd = a.row[w + 1] - a.row[w];
+            ++nf;
+            mf += wd;
+          }
+        }
+        warp_enqueue(disc, w, wd, a, nxt, ctl->next_bin_n);
       }
-      const int32_t ov = __shfl_sync(FULL, v, owner);
-      const int64_t ors = __shfl_sync(FULL, rs, owner);
-      const int32_t oex = __shfl_sync(FULL, excl, owner);
-      bool disc = false;
-      int32_t w = 0;
-      int64_t wd = 0;
-      if (idx < total) {
-        w = a.col[ors + (idx - oex)];
-        disc = td_visit(a.state, vis, w, hi | (uint32_t)ov);
-        if (disc) wd = a.row[w + 1] - a.row[w];
-      }
-      warp_enqueue(disc, w, wd, nq, ctl);
     }
   }
-  add_examined(a, examined);
-}
-
-__global__ void __launch_bounds__(BFS_THREADS) bfs_td_grid(BfsArgs a) {
-  BfsCtl* ctl = a.ctl;
-  const int64_t nbig = ctl->big_n;
-  if (nbig == 0) return;
-  const int cur = ctl->cur;
-  int32_t* __restrict__ nq = cur ? a.q0 : a.q1;
-  uint32_t* vis = ctl->vcur ? a.vis1 : a.vis0;
-  const uint64_t hi = (uint64_t)(uint32_t)(ctl->level + 1) << 32;
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = gtid() >> 5, nw = gthreads() >> 5;
-  int64_t examined = 0;
-  for (int64_t j = 0; j < nbig; ++j) {
-    const int32_t v = a.big[j];
-    const int64_t s = a.row[v], e = a.row[v + 1];
-    const uint64_t packed = hi | (uint32_t)v;
-    for (int64_t k0 = s + gw * 32; k0 < e; k0 += nw * 32) {
-      const int64_t k = k0 + lane;
-      bool disc = false;
-      int32_t w = 0;
-      int64_t wd = 0;
-      if (k < e) {
-        w = a.col[k];
-        disc = td_visit(a.state, vis, w, packed);
-        if (disc) wd = a.row[w + 1] - a.row[w];
-        ++examined;
-      }
-      warp_enqueue(disc, w, wd, nq, ctl);
-    }
-  }
-  add_examined(a, examined);
+  block_commit(a, nf, mf, examined);
 }
 
 // Sets the visited bits of the current frontier (needed before a bottom-up step that
 // follows a top-down one: top-down leaves its discoveries unmarked until they expand).
 __global__ void bfs_mark(BfsArgs a) {
   BfsCtl* ctl = a.ctl;
-  const int32_t* __restrict__ q = ctl->cur ? a.q1 : a.q0;
   uint32_t* vis = ctl->vcur ? a.vis1 : a.vis0;
-  const int64_t nf = ctl->n_f;
-  for (int64_t i = gtid(); i < nf; i += gthreads()) {
-    const int32_t v = q[i];
-    atomicOr(&vis[v >> 5], 1u << (v & 31));
+  for (int b = 0; b < NBINS; ++b) {
+    const int32_t* __restrict__ q = queue_of(a, ctl->cur, b);
+    const int64_t nb = ctl->bin_n[b];
+    for (int64_t i = gtid(); i < nb; i += gthreads()) {
+      const int32_t v = q[i];
+      atomicOr(&vis[v >> 5], 1u << (v & 31));
+    }
+  }
+}
+
+// Rebuilds the binned frontier queue of the current level from the two bitmaps (vertices
+// visited now but not before the last bottom-up step) when top-down follows bottom-up.
+// A lane takes one word; the warp enqueues round by round, each lane contributing its
+// next set bit, so a sparse frontier costs one pass over the words.
+__global__ void __launch_bounds__(BFS_THREADS) bfs_queue_from_bitmap(BfsArgs a) {
+  BfsCtl* ctl = a.ctl;
+  const uint32_t* __restrict__ vnew = ctl->vcur ? a.vis1 : a.vis0;
+  const uint32_t* __restrict__ vold = ctl->vcur ? a.vis0 : a.vis1;
+  const int cur = ctl->cur;
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = gtid() >> 5, nw = gthreads() >> 5;
+  for (int64_t w0 = gw * 32; w0 < a.nwords; w0 += nw * 32) {
+    uint32_t f = vnew[w0 + lane] & ~vold[w0 + lane];
+    while (__any_sync(FULL, f != 0)) {
+      const bool has = f != 0;
+      int32_t v = 0;
+      int64_t d = 0;
+      if (has) {
+        v = (int32_t)((w0 + lane) * 32 + __ffs(f) - 1);
+        f &= f - 1;
+        d = a.row[v + 1] - a.row[v];
+      }
+      warp_enqueue(has, v, d, a, cur, ctl->bin_n);
+    }
   }
 }
 
 // ---- bottom-up ---------------------------------------------------------------------
-// A warp takes 128 bitmap words (4096 vertices) with one 128-bit load per lane. For each
-// of the lane's 4 words in turn, the warp compacts the unvisited vertices (popc + warp
-// prefix sum) into a shared list; lanes then take one listed vertex each and check its
-// first bu_scan neighbours alone; vertices still open after that are taken over by the
-// whole warp, 32 neighbours per step, first hit by ballot. Found vertices set bits in a
-// shared copy of the 128 words, written once to the next bitmap (Alg. 5's single write
-// per block).
-__global__ void __launch_bounds__(BFS_THREADS) bfs_bu(BfsArgs a) {
-  __shared__ uint16_t slist[WARPS][1024];
-  __shared__ uint32_t sfound[WARPS][BU_CHUNK_WORDS];
+// Gather: a warp reads 128 visited words with one 128-bit load per lane, copies them to
+// the next bitmap, and compacts the unvisited vertices (popc + warp sum for the
+// reservation, then one ballot per word so each word's vertices are written by
+// consecutive lanes) into a global list in ascending order (Alg. 5's block search: a
+// fully visited block costs one load).
+__global__ void __launch_bounds__(BFS_THREADS) bfs_bu_gather(BfsArgs a) {
   BfsCtl* ctl = a.ctl;
-  const uint32_t* __restrict__ vc = ctl->vcur ? a.vis1 : a.vis0;
-  uint32_t* __restrict__ vn = ctl->vcur ? a.vis0 : a.vis1;
-  int32_t* __restrict__ nq = ctl->cur ? a.q0 : a.q1;
-  const uint64_t hi = (uint64_t)(uint32_t)(ctl->level + 1) << 32;
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const uint4* __restrict__ vc = reinterpret_cast<const uint4*>(ctl->vcur ? a.vis1 : a.vis0);
+  uint4* __restrict__ vn = reinterpret_cast<uint4*>(ctl->vcur ? a.vis0 : a.vis1);
+  const int lane = threadIdx.x & 31;
   const int64_t gw = gtid() >> 5, nw = gthreads() >> 5;
   const int64_t nchunks = a.nwords / BU_CHUNK_WORDS;
-  uint16_t* list = slist[wp];
-  uint32_t* found = sfound[wp];
-  int64_t examined = 0;
   for (int64_t c = gw; c < nchunks; c += nw) {
-    const uint4 w4 = __ldg(reinterpret_cast<const uint4*>(vc) + c * 32 + lane);
-    found[lane * 4 + 0] = 0;
-    found[lane * 4 + 1] = 0;
-    found[lane * 4 + 2] = 0;
-    found[lane * 4 + 3] = 0;
-    const unsigned any = __ballot_sync(FULL, (w4.x & w4.y & w4.z & w4.w) != 0xFFFFFFFFu);
-    if (any) {
-      __syncwarp();
-      const int64_t vbase = c * (BU_CHUNK_WORDS * 32);
-#pragma unroll 1
+    const uint4 w4 = __ldg(vc + c * 32 + lane);
+    vn[c * 32 + lane] = w4;
+    const uint32_t u0 = ~w4.x, u1 = ~w4.y, u2 = ~w4.z, u3 = ~w4.w;
+    const int cnt = __popc(u0) + __popc(u1) + __popc(u2) + __popc(u3);
+    const int total = warp_sum(cnt);
+    if (total == 0) continue;
+    unsigned long long p = 0;
+    if (lane == 0) p = atomicAdd((unsigned long long*)&ctl->ulist_n, (unsigned long long)total);
+    p = __shfl_sync(FULL, p, 0);
+    unsigned lanes = __ballot_sync(FULL, cnt != 0);
+    while (lanes) {
+      const int j = __ffs(lanes) - 1;
+      lanes &= lanes - 1;
+#pragma unroll
       for (int k = 0; k < 4; ++k) {
-        uint32_t un = ~(k == 0 ? w4.x : k == 1 ? w4.y : k == 2 ? w4.z : w4.w);
-        const int cnt = __popc(un);
-        const int incl = warp_incl_scan(cnt);
-        const int total = __shfl_sync(FULL, incl, 31);
-        if (total == 0) continue;
-        int pos = incl - cnt;
-        const int wl = lane * 4 + k;
-        while (un) {
-          const int b = __ffs(un) - 1;
-          un &= un - 1;
-          list[pos++] = (uint16_t)(wl * 32 + b);
-        }
-        __syncwarp();
-        for (int t0 = 0; t0 < total; t0 += 32) {
-          const int t = t0 + lane;
-          const bool act = t < total;
-          const int32_t loc = act ? list[t] : 0;
-          const int32_t w = (int32_t)(vbase + loc);
-          int64_t s = 0, e = 0;
-          if (act) {
-            s = a.row[w];
-            e = a.row[w + 1];
-          }
-          const int64_t lim = min(e, s + (int64_t)a.bu_scan);
-          int32_t par = -1;
-          int64_t kk = s;
-          for (; kk < lim; ++kk) {
-            const int32_t u = a.col[kk];
-            if ((__ldg(&vc[u >> 5]) >> (u & 31)) & 1u) {
-              par = u;
-              break;
-            }
-          }
-          examined += (par >= 0 ? kk + 1 : kk) - s;
-          const bool fnd = par >= 0;
-          if (fnd) {
-            a.state[w] = hi | (uint32_t)par;
-            atomicOr(&found[loc >> 5], 1u << (loc & 31));
-          }
-          warp_enqueue(fnd, w, e - s, nq, ctl);
-          unsigned lm = __ballot_sync(FULL, act && !fnd && lim < e);
-          while (lm) {
-            const int src = __ffs(lm) - 1;
-            lm &= lm - 1;
-            const int32_t w2 = __shfl_sync(FULL, w, src);
-            const int32_t loc2 = __shfl_sync(FULL, loc, src);
-            const int64_t s2 = __shfl_sync(FULL, lim, src), e2 = __shfl_sync(FULL, e, src);
-            const int64_t d2 = e2 - __shfl_sync(FULL, s, src);
-            int32_t par2 = -1;
-            for (int64_t b0 = s2; b0 < e2; b0 += 32) {
-              const int64_t k2 = b0 + lane;
-              int32_t u = 0;
-              bool hit = false;
-              if (k2 < e2) {
-                u = a.col[k2];
-                hit = (__ldg(&vc[u >> 5]) >> (u & 31)) & 1u;
-              }
-              const unsigned hm = __ballot_sync(FULL, hit);
-              if (lane == 0) examined += hm ? (__ffs(hm)) : min((int64_t)32, e2 - b0);
-              if (hm) {
-                par2 = __shfl_sync(FULL, u, __ffs(hm) - 1);
-                break;
-              }
-            }
-            if (par2 >= 0 && lane == 0) {
-              a.state[w2] = hi | (uint32_t)par2;
-              atomicOr(&found[loc2 >> 5], 1u << (loc2 & 31));
-              const unsigned long long p = atomicAdd((unsigned long long*)&ctl->next_n, 1ull);
-              atomicAdd((unsigned long long*)&ctl->next_m, (unsigned long long)d2);
-              nq[p] = w2;
-            }
-          }
-        }
-        __syncwarp();
+        const uint32_t word = __shfl_sync(FULL, k == 0 ? u0 : k == 1 ? u1 : k == 2 ? u2 : u3, j);
+        if (word == 0) continue;
+        const bool bit = (word >> lane) & 1u;
+        const unsigned m = __ballot_sync(FULL, bit);
+        if (bit) a.ulist[p + __popc(m & lanemask_lt())] = (int32_t)((((c * 32 + j) * 4 + k) << 5) + lane);
+        p += __popc(m);
       }
     }
-    __syncwarp();
-    uint4 o;
-    o.x = w4.x | found[lane * 4 + 0];
-    o.y = w4.y | found[lane * 4 + 1];
-    o.z = w4.z | found[lane * 4 + 2];
-    o.w = w4.w | found[lane * 4 + 3];
-    reinterpret_cast<uint4*>(vn)[c * 32 + lane] = o;
-    __syncwarp();
   }
-  add_examined(a, examined);
+}
+
+constexpr int BU_V = 4;  // listed vertices a lane keeps in flight
+
+__device__ __forceinline__ bool visited_bit(const uint32_t* __restrict__ vc, int32_t u) {
+  return (__ldg(&vc[u >> 5]) >> (u & 31)) & 1u;
+}
+
+// Scan: a warp takes 32 x BU_V consecutive listed vertices; each lane issues the row and
+// first-neighbour loads of its BU_V vertices together, then checks up to bu_thread_scan
+// neighbours per vertex alone, in ascending order, stopping at the first visited one.
+// Vertices still open are taken over by the whole warp, 32 neighbours per step, first hit
+// by ballot. A found vertex records (L+1, parent) and sets its bit in the next bitmap
+// (one atomic per distinct word); counts are committed once per CTA. The frontier
+// queue is not written here: the next bottom-up step reads the bitmap, and a top-down
+// step rebuilds the queue from the bitmaps first.
+__global__ void __launch_bounds__(BFS_THREADS) bfs_bu_scan(BfsArgs a) {
+  BfsCtl* ctl = a.ctl;
+  const uint32_t* __restrict__ vc = ctl->vcur ? a.vis1 : a.vis0;
+  uint32_t* vn = ctl->vcur ? a.vis0 : a.vis1;
+  const uint64_t hi = (uint64_t)(uint32_t)(ctl->level + 1) << 32;
+  const int64_t nu = ctl->ulist_n;
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = gtid() >> 5, nw = gthreads() >> 5;
+  const int64_t span = 32 * BU_V;
+  int64_t nf = 0, mf = 0, examined = 0;
+  for (int64_t base = gw * span; base < nu; base += nw * span) {
+    int32_t w[BU_V], par[BU_V];
+    int64_t s[BU_V], e[BU_V], lim[BU_V];
+#pragma unroll
+    for (int j = 0; j < BU_V; ++j) {
+      const int64_t i = base + j * 32 + lane;
+      w[j] = i < nu ? a.ulist[i] : -1;
+    }
+#pragma unroll
+    for (int j = 0; j < BU_V; ++j) {
+      s[j] = 0;
+      e[j] = 0;
+      if (w[j] >= 0) {
+        s[j] = a.row[w[j]];
+        e[j] = a.row[w[j] + 1];
+      }
+    }
+    int32_t u0[BU_V];
+#pragma unroll
+    for (int j = 0; j < BU_V; ++j) u0[j] = (s[j] < e[j]) ? a.col[s[j]] : -1;
+#pragma unroll
+    for (int j = 0; j < BU_V; ++j) {
+      par[j] = (u0[j] >= 0 && visited_bit(vc, u0[j])) ? u0[j] : -1;
+      lim[j] = min(e[j], s[j] + (int64_t)max(a.bu_scan, 1));
+      int64_t k = s[j] + 1;
+      if (par[j] < 0) {
+        for (; k < lim[j]; ++k) {
+          const int32_t u = a.col[k];
+          if (visited_bit(vc, u)) {
+            par[j] = u;
+            ++k;
+            break;
+          }
+        }
+      }
+      examined += min(k, e[j]) - s[j];
+    }
+#pragma unroll
+    for (int j = 0; j < BU_V; ++j) {
+      const bool fnd = par[j] >= 0;
+      if (fnd) {
+        a.state[w[j]] = hi | (uint32_t)par[j];
+        ++nf;
+        mf += e[j] - s[j];
+      }
+      const unsigned peers = __match_any_sync(FULL, fnd ? (w[j] >> 5) : -1);
+      const unsigned bits = __reduce_or_sync(peers, fnd ? (1u << (w[j] & 31)) : 0u);
+      if (fnd && lane == __ffs(peers) - 1) atomicOr(&vn[w[j] >> 5], bits);
+      unsigned lm = __ballot_sync(FULL, w[j] >= 0 && !fnd && lim[j] < e[j]);
+      while (lm) {
+        const int src = __ffs(lm) - 1;
+        lm &= lm - 1;
+        const int32_t w2 = __shfl_sync(FULL, w[j], src);
+        const int64_t s2 = __shfl_sync(FULL, lim[j], src), e2 = __shfl_sync(FULL, e[j], src);
+        const int64_t d2 = e2 - __shfl_sync(FULL, s[j], src);
+        int32_t par2 = -1;
+        for (int64_t b0 = s2; b0 < e2; b0 += 32) {
+          const int64_t k2 = b0 + lane;
+          int32_t u = 0;
+          bool hit = false;
+          if (k2 < e2) {
+            u = a.col[k2];
+            hit = visited_bit(vc, u);
+          }
+          const unsigned hm = __ballot_sync(FULL, hit);
+          if (lane == 0) examined += hm ? __ffs(hm) : min((int64_t)32, e2 - b0);
+          if (hm) {
+            par2 = __shfl_sync(FULL, u, __ffs(hm) - 1);
+            break;
+          }
+        }
+        if (par2 >= 0 && lane == 0) {
+          a.state[w2] = hi | (uint32_t)par2;
+          atomicOr(&vn[w2 >> 5], 1u << (w2 & 31));
+          ++nf;
+          mf += d2;
+        }
+      }
+    }
+  }
+  block_commit(a, nf, mf, examined);
 }
 
 // ---- level control -----------------------------------------------------------------
-// After each step: record the trace, swap queues (and bitmaps after bottom-up), and pick
-// the next direction by the frontier-size rule of Beamer et al. (the paper's reference
-// [12]; Alg. 1 calls it is_top_down_direction): top-down -> bottom-up when
+// After each step: record the trace, swap queue sets (and bitmaps after bottom-up), and
+// pick the next direction by the frontier-size rule of Beamer et al. (the paper's
+// reference [12]; Alg. 1 calls it is_top_down_direction): top-down -> bottom-up when
 // m_f * alpha > m_u, bottom-up -> top-down when n_f * beta < n and the frontier shrank.
 __global__ void bfs_decide(BfsArgs a, cudaGraphConditionalHandle h_loop, int use_handles) {
   BfsCtl* c = a.ctl;
@@ -372,9 +526,13 @@ __global__ void bfs_decide(BfsArgs a, cudaGraphConditionalHandle h_loop, int use
     c->prev_n_f = c->n_f;
     c->n_f = nn;
     c->m_f = nm;
+    for (int b = 0; b < NBINS; ++b) {
+      c->bin_n[b] = dir == DIR_TD ? c->next_bin_n[b] : 0;  // bottom-up fills no queue
+      c->next_bin_n[b] = 0;
+    }
     c->next_n = 0;
     c->next_m = 0;
-    c->big_n = 0;
+    c->ulist_n = 0;
     c->examined = 0;
     c->cur ^= 1;
     if (dir == DIR_BU) c->vcur ^= 1;
@@ -392,14 +550,22 @@ __global__ void bfs_decide(BfsArgs a, cudaGraphConditionalHandle h_loop, int use
       if (nn * (int64_t)c->beta < a.n && nn < c->prev_n_f) nd = DIR_TD;
     }
     c->need_mark = (dir == DIR_TD && nd == DIR_BU);
+    c->need_queue = (dir == DIR_BU && nd == DIR_TD);
     c->dir = nd;
   }
   if (use_handles) cudaGraphSetConditional(h_loop, c->done ? 0u : 1u);
 }
 
+// Which step kernels run next: 0 top-down, 1 bottom-up, 2 mark + bottom-up,
+// 3 queue rebuild + top-down.
+__device__ __forceinline__ unsigned step_kind(const BfsCtl* c) {
+  if (c->dir == DIR_TD) return c->need_queue ? 3u : 0u;
+  return c->need_mark ? 2u : 1u;
+}
+
 // First node of each loop iteration: routes the switch to the step now due.
 __global__ void bfs_select(BfsCtl* c, cudaGraphConditionalHandle h_dir) {
-  cudaGraphSetConditional(h_dir, c->dir == DIR_TD ? 0u : (c->need_mark ? 2u : 1u));
+  cudaGraphSetConditional(h_dir, step_kind(c));
 }
 
 // Clears the traversal state: state = UNVISITED, visited bitmap 0 except the padding
@@ -426,10 +592,15 @@ __device__ void ctl_begin(const BfsArgs& a, int32_t start, int32_t start_level, 
   c->vcur = 0;
   c->nlevels = 0;
   c->err = 0;
+  for (int b = 0; b < NBINS; ++b) {
+    c->bin_n[b] = 0;
+    c->next_bin_n[b] = 0;
+  }
   c->next_n = 0;
   c->next_m = 0;
   c->examined = 0;
-  c->big_n = 0;
+  c->ulist_n = 0;
+  c->need_queue = 0;
   c->alpha = alpha;
   c->beta = beta;
   c->force = force;
@@ -450,7 +621,9 @@ __device__ void ctl_begin(const BfsArgs& a, int32_t start, int32_t start_level, 
   const int64_t d = a.row[start + 1] - a.row[start];
   a.state[start] = ((uint64_t)(uint32_t)start_level << 32) | (uint32_t)start;
   a.vis0[start >> 5] |= 1u << (start & 31);
-  a.q0[0] = start;
+  const int b = bin_of(a, d);
+  queue_of(a, 0, b)[0] = start;
+  c->bin_n[b] = 1;
   c->n_f = 1;
   c->m_f = d;
   c->m_u = a.nnz - d;
@@ -465,7 +638,6 @@ struct EtArgs {
   const int32_t* up;
   const int32_t* old2core;
   const int32_t* new2old;
-  int32_t* epoch;
   int64_t n;
 };
 
@@ -495,7 +667,8 @@ __global__ void et_start(BfsArgs a, EtArgs e, int32_t root, int32_t alpha, int32
 
 // Levels and parents of every vertex in vertex-id order: core vertices from the core
 // BFS state (parents back to vertex ids), edge-tree vertices hanging from a core vertex
-// from that vertex's level (Alg. 7 / Alg. 10 with levels), everything else -1.
+// from that vertex's level (Alg. 7 / Alg. 10 with levels), tree vertices hanging from a
+// tree vertex -2 ("resolve pending", see et_resolve), everything else -1.
 __global__ void et_output(EtArgs e, const uint64_t* __restrict__ state, int32_t* __restrict__ parent,
                           int32_t* __restrict__ level) {
   for (int64_t v = gtid(); v < e.n; v += gthreads()) {
@@ -507,6 +680,9 @@ __global__ void et_output(EtArgs e, const uint64_t* __restrict__ state, int32_t*
         l = (int32_t)(s >> 32);
         p = e.new2old[(uint32_t)s];
       }
+    } else if (info == INT32_MIN) {
+      l = -2;
+      p = -2;
     } else if (info <= -2) {
       const int32_t cu = -2 - info;
       const uint64_t s = state[cu];
@@ -522,14 +698,12 @@ __global__ void et_output(EtArgs e, const uint64_t* __restrict__ state, int32_t*
 
 // Root on an edge tree: the vertices on the walk from the root to the core get their
 // levels and parents from the walk (direction reversed: parent = the previous vertex),
-// and the core vertex reached takes the last tree vertex as parent. Walk vertices are
-// marked with this traversal's epoch so the tree-up resolution pass leaves them alone.
-__global__ void et_fixup(EtArgs e, int32_t root, int32_t ep, int32_t* __restrict__ parent,
-                         int32_t* __restrict__ level) {
+// and the core vertex reached takes the last tree vertex as parent. Walk vertices then
+// hold levels >= 0, so the resolution pass (which only fills -2 entries) leaves them.
+__global__ void et_fixup(EtArgs e, int32_t root, int32_t* __restrict__ parent, int32_t* __restrict__ level) {
   if (e.vinfo[root] >= 0) return;
   level[root] = 0;
   parent[root] = root;
-  e.epoch[root] = ep;
   int32_t v = root, k = 0;
   for (int64_t guard = 0; guard < e.n; ++guard) {
     const int32_t u = e.up[v];
@@ -541,19 +715,17 @@ __global__ void et_fixup(EtArgs e, int32_t root, int32_t ep, int32_t* __restrict
     ++k;
     level[u] = k;
     parent[u] = v;
-    e.epoch[u] = ep;
     v = u;
   }
 }
 
 // Tree vertices hanging from another tree vertex, one height at a time from the top:
-// level = level(up) + 1 (Alg. 10 with levels).
+// level = level(up) + 1 (Alg. 10 with levels), for entries still at -2.
 __global__ void et_resolve(const int32_t* __restrict__ list, const int32_t* __restrict__ lup, int64_t b, int64_t e,
-                           const int32_t* __restrict__ epoch, int32_t ep, int32_t* __restrict__ parent,
-                           int32_t* __restrict__ level) {
+                           int32_t* __restrict__ parent, int32_t* __restrict__ level) {
   for (int64_t i = b + gtid(); i < e; i += gthreads()) {
     const int32_t v = list[i];
-    if (epoch[v] == ep) continue;
+    if (level[v] != -2) continue;
     const int32_t u = lup[i];
     const int32_t lu = level[u];
     level[v] = lu >= 0 ? lu + 1 : -1;
@@ -577,8 +749,22 @@ int grid_stream(const gt_graph* g, int64_t work) {
   return (int)std::max<int64_t>(1, std::min(want, cap));
 }
 
+// The step kernels of one level: 0 top-down, 1 bottom-up (gather + scan), 2 mark +
+// bottom-up, 3 queue rebuild + top-down.
+void launch_step(int kind, const BfsArgs& a, int grid, cudaStream_t s) {
+  if (kind == 3) bfs_queue_from_bitmap<<<grid, BFS_THREADS, 0, s>>>(a);
+  if (kind == 0 || kind == 3) {
+    bfs_td<<<grid, BFS_THREADS, 0, s>>>(a);
+    return;
+  }
+  if (kind == 2) bfs_mark<<<grid, BFS_THREADS, 0, s>>>(a);
+  bfs_bu_gather<<<grid, BFS_THREADS, 0, s>>>(a);
+  bfs_bu_scan<<<grid, BFS_THREADS, 0, s>>>(a);
+}
+
 // Builds the CUDA graph of the level loop for one view:
-//   WHILE(loop) { select -> SWITCH(dir) { 0: td, td_grid | 1: bu | 2: mark, bu } -> decide }
+//   WHILE(loop) { select -> SWITCH(kind) { 0: td | 1: gather, scan | 2: mark, gather, scan |
+//                                          3: queue, td } -> decide }
 // The while handle (created on the top graph, default 1) is set by decide; the switch
 // handle belongs to the body graph, which holds its node, and is set by select.
 int build_loop_graph(gt_graph* g, const View& v, cudaGraphExec_t* out) {
@@ -617,28 +803,22 @@ int build_loop_graph(gt_graph* g, const View& v, cudaGraphExec_t* out) {
     kp.kernelParams = args;
     fail(cudaGraphAddKernelNode(&sel, body, nullptr, 0, &kp), "select node");
   }
-  cudaGraph_t branch[3] = {nullptr, nullptr, nullptr};
+  cudaGraph_t branch[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaGraphNode_t sw = nullptr;
   if (rc == GT_OK) {
     cudaGraphNodeParams np{};
     np.type = cudaGraphNodeTypeConditional;
     np.conditional.handle = h_dir;
     np.conditional.type = cudaGraphCondTypeSwitch;
-    np.conditional.size = 3;
+    np.conditional.size = 4;
     fail(cudaGraphAddNode(&sw, body, &sel, nullptr, 1, &np), "switch node");
     if (rc == GT_OK)
-      for (int i = 0; i < 3; ++i) branch[i] = np.conditional.phGraph_out[i];
+      for (int i = 0; i < 4; ++i) branch[i] = np.conditional.phGraph_out[i];
   }
-  for (int i = 0; i < 3 && rc == GT_OK; ++i) {
+  for (int i = 0; i < 4 && rc == GT_OK; ++i) {
     fail(cudaStreamBeginCaptureToGraph(cs, branch[i], nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed), "capture");
     if (rc != GT_OK) break;
-    if (i == 0) {
-      bfs_td<<<grid, BFS_THREADS, 0, cs>>>(a);
-      bfs_td_grid<<<grid, BFS_THREADS, 0, cs>>>(a);
-    } else {
-      if (i == 2) bfs_mark<<<grid, BFS_THREADS, 0, cs>>>(a);
-      bfs_bu<<<grid, BFS_THREADS, 0, cs>>>(a);
-    }
+    launch_step(i, a, grid, cs);
     cudaGraph_t got = nullptr;
     fail(cudaStreamEndCapture(cs, &got), "end capture");
   }
@@ -674,7 +854,7 @@ int run_level_loop(gt_graph* g, View& v, int which, cudaStream_t s) {
   const BfsArgs a = make_args(v, t);
   const int grid = g->launch.grid;
   struct Head {
-    int32_t level, dir, done, cur, vcur, need_mark;
+    int32_t level, dir, done, cur, vcur, need_mark, need_queue;
   } h{};
   const cudaGraphConditionalHandle none = 0;
   int timed_steps = 0;
@@ -694,13 +874,7 @@ int run_level_loop(gt_graph* g, View& v, int which, cudaStream_t s) {
       }
       cudaEventRecord(g->step_events[2 * guard], s);
     }
-    if (h.dir == DIR_TD) {
-      bfs_td<<<grid, BFS_THREADS, 0, s>>>(a);
-      bfs_td_grid<<<grid, BFS_THREADS, 0, s>>>(a);
-    } else {
-      if (h.need_mark) bfs_mark<<<grid, BFS_THREADS, 0, s>>>(a);
-      bfs_bu<<<grid, BFS_THREADS, 0, s>>>(a);
-    }
+    launch_step(h.dir == DIR_TD ? (h.need_queue ? 3 : 0) : (h.need_mark ? 2 : 1), a, grid, s);
     if (timed) {
       cudaEventRecord(g->step_events[2 * guard + 1], s);
       ++timed_steps;
@@ -727,7 +901,7 @@ int run_bfs(gt_graph* g, View& v, bool et, int64_t root, int32_t* parent, int32_
   const BfsArgs a = make_args(v, t);
   const int gs = grid_stream(g, std::max<int64_t>(v.n, v.nwords));
   bfs_reset<<<gs, 256, 0, s>>>(v.state, v.vis[0], v.n, v.nwords);
-  EtArgs e{g->vinfo, g->up, g->old2core, g->new2old, g->epoch, g->n};
+  EtArgs e{g->vinfo, g->up, g->old2core, g->new2old, g->n};
   if (et)
     et_start<<<1, 1, 0, s>>>(a, e, (int32_t)root, t.alpha, t.beta, t.force_direction);
   else
@@ -739,16 +913,11 @@ int run_bfs(gt_graph* g, View& v, bool et, int64_t root, int32_t* parent, int32_
   if (et) {
     const int go = grid_stream(g, g->n);
     et_output<<<go, 256, 0, s>>>(e, v.state, parent, level);
-    if (++g->cur_epoch <= 0) {  // wrapped: clear the marks
-      cudaMemsetAsync(g->epoch, 0, sizeof(int32_t) * g->n, s);
-      g->cur_epoch = 1;
-    }
-    et_fixup<<<1, 1, 0, s>>>(e, (int32_t)root, g->cur_epoch, parent, level);
+    et_fixup<<<1, 1, 0, s>>>(e, (int32_t)root, parent, level);
     for (int h = 0; h < g->resolve_heights; ++h) {
       const int64_t b = g->resolve_ptr_host[h], en = g->resolve_ptr_host[h + 1];
       if (en > b)
-        et_resolve<<<grid_stream(g, en - b), 256, 0, s>>>(g->resolve_list, g->resolve_up, b, en, g->epoch,
-                                                           g->cur_epoch, parent, level);
+        et_resolve<<<grid_stream(g, en - b), 256, 0, s>>>(g->resolve_list, g->resolve_up, b, en, parent, level);
     }
   } else {
     plain_output<<<grid_stream(g, v.n), 256, 0, s>>>(v.state, v.n, parent, level);

@@ -249,8 +249,8 @@ __global__ void core_fill(const int64_t* __restrict__ row, const int32_t* __rest
 // ---- a4: edge-tree layout -----------------------------------------------------------
 
 // vinfo: core id for core vertices; -2 - (core id of up) for tree vertices hanging from
-// a core vertex; -1 for the rest (zero-degree vertices, tree tops, tree vertices
-// hanging from another tree vertex). rflag marks the last group for the resolve list.
+// a core vertex; INT32_MIN for tree vertices hanging from another tree vertex (resolved
+// height by height, listed through rflag); -1 for the rest (zero-degree vertices, tops).
 __global__ void tree_info(int64_t n, const uint8_t* __restrict__ vtype, const int32_t* __restrict__ up,
                           const int32_t* __restrict__ old2core, int32_t* __restrict__ vinfo,
                           uint8_t* __restrict__ rflag) {
@@ -264,10 +264,12 @@ __global__ void tree_info(int64_t n, const uint8_t* __restrict__ vtype, const in
       const int32_t u = up[v];
       if (u >= 0) {
         const int32_t cu = old2core[u];
-        if (cu >= 0)
+        if (cu >= 0) {
           info = -2 - cu;
-        else
+        } else {
+          info = INT32_MIN;
           f = 1;
+        }
       }
     }
     vinfo[v] = info;
@@ -342,22 +344,19 @@ int alloc_view_state(gt_graph* g, View& v, cudaStream_t s) {
   v.nwords = (v.nwords + BU_CHUNK_WORDS - 1) / BU_CHUNK_WORDS * BU_CHUNK_WORDS;
   int rc;
   if ((rc = device_malloc(g, (void**)&v.state, sizeof(uint64_t) * n))) return rc;
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < 2; ++i)
     if ((rc = device_malloc(g, (void**)&v.vis[i], sizeof(uint32_t) * v.nwords))) return rc;
-    if ((rc = device_malloc(g, (void**)&v.queue[i], sizeof(int32_t) * n))) return rc;
-  }
-  if ((rc = device_malloc(g, (void**)&v.big, sizeof(int32_t) * n))) return rc;
+  if ((rc = device_malloc(g, (void**)&v.queues, sizeof(int32_t) * n * 2 * NBINS))) return rc;
+  if ((rc = device_malloc(g, (void**)&v.ulist, sizeof(int32_t) * n))) return rc;
   if ((rc = device_malloc(g, (void**)&v.ctl, sizeof(BfsCtl)))) return rc;
   return GT_OK;
 }
 
 static void free_view(View& v) {
   cudaFree(v.state);
-  for (int i = 0; i < 2; ++i) {
-    cudaFree(v.vis[i]);
-    cudaFree(v.queue[i]);
-  }
-  cudaFree(v.big);
+  for (int i = 0; i < 2; ++i) cudaFree(v.vis[i]);
+  cudaFree(v.queues);
+  cudaFree(v.ulist);
   cudaFree(v.ctl);
   v = View{};
 }
@@ -381,7 +380,8 @@ void free_graph(gt_graph* g) {
   cudaFree(g->vinfo);
   cudaFree(g->new2old);
   cudaFree(g->old2core);
-  cudaFree(g->epoch);
+  free_batch_mem(g);
+  cudaFree(g->batch_dev);
   cudaFree(g->resolve_list);
   cudaFree(g->resolve_up);
   cudaFree(g->scratch_out);
@@ -564,8 +564,6 @@ int build_graph(gt_graph* g, const int64_t* edges, int64_t m, int64_t n, cudaStr
 
   // ---- a4: tree layout
   TRY(device_malloc(g, (void**)&g->vinfo, sizeof(int32_t) * n));
-  TRY(device_malloc(g, (void**)&g->epoch, sizeof(int32_t) * n));
-  TRYC(cudaMemsetAsync(g->epoch, 0, sizeof(int32_t) * n, s), "memset");
   uint8_t* rflag = is_core;  // is_core is consumed; reuse its storage
   tree_info<<<gn, BT, 0, s>>>(n, g->vtype, g->up, g->old2core, g->vinfo, rflag);
   TRY(scan_u8_to_i32(rflag, pos, n, s, d_scan, scan_bytes));

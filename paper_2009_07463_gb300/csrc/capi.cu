@@ -50,7 +50,7 @@ int where(const void* p) {
 }
 
 void apply_launch(gt_graph* g) {
-  int bpm = g->tuning.blocks_per_sm > 0 ? g->tuning.blocks_per_sm : 4;
+  int bpm = g->tuning.blocks_per_sm > 0 ? g->tuning.blocks_per_sm : 8;
   g->launch.grid = g->launch.sms * bpm;
 }
 
@@ -133,13 +133,16 @@ GT_API void gt_tuning_default(gt_tuning* t) {
   t->alpha = 14;
   t->beta = 24;
   t->td_warp_min = 32;
-  t->td_grid_min = 4096;
+  t->td_cta_min = 256;
+  t->td_grid_min = 2048;
   t->bu_thread_scan = 8;
-  t->blocks_per_sm = 4;
+  t->blocks_per_sm = 8;
   t->force_direction = 0;
   t->launch_mode = 0;
   t->count_work = 0;
   t->time_kernels = 0;
+  t->batch_alpha = 14;
+  t->batch_beta = 24;
 }
 
 GT_API int gt_graph_build(const int64_t* edges, int64_t m, int64_t n, const gt_config* cfg, void* stream,
@@ -216,10 +219,12 @@ GT_API int gt_graph_get_tuning(gt_graph_t g, gt_tuning* out) {
 
 GT_API int gt_graph_set_tuning(gt_graph_t g, const gt_tuning* t) {
   if (!g || !t) return GT_EINVAL;
-  if (t->alpha < 1 || t->beta < 1 || t->td_warp_min < 1 || t->td_grid_min < t->td_warp_min ||
+  if (t->alpha < 1 || t->beta < 1 || t->td_warp_min < 1 || t->td_cta_min < t->td_warp_min ||
+      t->td_grid_min < t->td_cta_min ||
       t->bu_thread_scan < 0 || t->blocks_per_sm < 1 || t->blocks_per_sm > 32 || t->force_direction < 0 ||
       t->force_direction > 2 || t->launch_mode < 0 || t->launch_mode > 1 || t->time_kernels < 0 ||
-      t->time_kernels > 1 || (t->time_kernels && t->launch_mode != 1)) {
+      t->time_kernels > 1 || (t->time_kernels && t->launch_mode != 1) || t->batch_alpha < 1 ||
+      t->batch_beta < 1) {
     set_error("gt_graph_set_tuning: value out of range");
     return GT_EINVAL;
   }
@@ -240,6 +245,47 @@ GT_API int gt_bfs(gt_graph_t g, int64_t root, int32_t* parent, int32_t* level, v
 
 GT_API int gt_bfs_plain(gt_graph_t g, int64_t root, int32_t* parent, int32_t* level, void* stream) {
   return bfs_common(g, false, root, parent, level, stream);
+}
+
+GT_API int gt_bfs_batch(const gt_graph_t* graphs, int32_t ngraphs, const int64_t* roots,
+                        const int32_t* roots_per_graph, int32_t* const* parent, int32_t* const* level,
+                        void* stream) {
+  if (!graphs || ngraphs < 1 || !roots_per_graph || !parent || !level) {
+    set_error("gt_bfs_batch: null argument or ngraphs < 1");
+    return GT_EINVAL;
+  }
+  int64_t total = 0;
+  for (int i = 0; i < ngraphs; ++i) {
+    if (!graphs[i] || roots_per_graph[i] < 0 || graphs[i]->device != graphs[0]->device) {
+      set_error("gt_bfs_batch: bad graph handle, negative root count or graphs on different devices");
+      return GT_EINVAL;
+    }
+    if (roots_per_graph[i] > 0 && (where(parent[i]) != 1 || where(level[i]) != 1)) {
+      set_error("gt_bfs_batch: outputs must be device memory");
+      return GT_EINVAL;
+    }
+    total += roots_per_graph[i];
+  }
+  if (total > 0 && !roots) return GT_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = cuda_fail(cudaSetDevice(graphs[0]->device), "cudaSetDevice");
+  if (rc) return rc;
+  for (int i = 0; i < ngraphs; ++i)
+    if (graphs[i]->last_stream && graphs[i]->last_stream != s) cudaStreamSynchronize(graphs[i]->last_stream);
+  rc = run_batch(graphs, ngraphs, roots, roots_per_graph, parent, level, s);
+  for (int i = 0; i < ngraphs; ++i) graphs[i]->last_stream = s;
+  return rc;
+}
+
+GT_API int gt_autotune(gt_graph_t g, int32_t nsample, uint64_t seed, gt_tuning* best, void* stream) {
+  if (!g || nsample < 1) return GT_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = cuda_fail(cudaSetDevice(g->device), "cudaSetDevice");
+  if (rc) return rc;
+  if (g->last_stream && g->last_stream != s) cudaStreamSynchronize(g->last_stream);
+  rc = autotune(g, nsample, seed, s, best);
+  g->last_stream = s;
+  return rc;
 }
 
 GT_API int gt_bfs_trace(gt_graph_t g, gt_level_info* out, int32_t cap, int32_t* nlevels) {

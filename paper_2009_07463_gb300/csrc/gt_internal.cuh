@@ -16,6 +16,10 @@ constexpr int DIR_TD = 0, DIR_BU = 1;
 constexpr int MAX_TRACE = 4096;
 constexpr int BFS_THREADS = 256;
 constexpr int BU_CHUNK_WORDS = 128;     // bitmap words one warp takes per step (4096 vertices)
+// Frontier queues are split by degree when a vertex is discovered, so the top-down step
+// can give each vertex the right amount of the machine: packed lanes (bin 0), a warp
+// (bin 1), a CTA (bin 2) or the whole grid (bin 3).
+constexpr int NBINS = 4;
 
 // Per-traversal control block in device memory. Kernels read the direction and buffer
 // selectors from here, so the level loop can run without the host (CUDA graph with a
@@ -24,24 +28,26 @@ struct BfsCtl {
   int32_t level;      // level of the current frontier
   int32_t dir;        // direction of the step now due
   int32_t done;       // 1 when the frontier is empty
-  int32_t cur;        // queue holding the current frontier (0/1)
+  int32_t cur;        // queue set holding the current frontier (0/1)
   int32_t vcur;       // visited bitmap that is current (0/1)
   int32_t need_mark;  // 1: set visited bits of the current queue before a bottom-up step
+  int32_t need_queue; // 1: rebuild the current queue from the bitmaps before a top-down step
   int32_t nlevels;    // steps taken
-  int32_t err;        // nonzero: a kernel found an inconsistency
   int64_t n_f;        // current frontier vertices
   int64_t m_f;        // their summed degree
   int64_t prev_n_f;
   int64_t m_u;        // summed degree of unvisited vertices
-  int64_t next_n;     // accumulators of the step in progress
-  int64_t next_m;
+  int64_t bin_n[NBINS];       // current frontier, per degree bin
+  int64_t next_bin_n[NBINS];  // next frontier being built, per degree bin
+  int64_t next_n;             // vertices of the next frontier
+  int64_t next_m;             // summed degree of the next frontier
   int64_t examined;
-  int64_t big_n;      // top-down: vertices handed to the whole grid
+  int64_t ulist_n;            // bottom-up: unvisited vertices gathered this step
   // traversal start (set by the start kernel)
   int32_t start;      // start vertex in the traversed graph's ids (-1: nothing to traverse)
   int32_t start_level;
   int32_t alpha, beta, force;
-  int32_t pad0;
+  int32_t err;        // nonzero: a kernel found an inconsistency
   gt_level_info trace[MAX_TRACE];
 };
 
@@ -54,8 +60,8 @@ struct View {
   int32_t* col = nullptr;
   uint64_t* state = nullptr;   // packed level/parent per vertex
   uint32_t* vis[2] = {nullptr, nullptr};
-  int32_t* queue[2] = {nullptr, nullptr};
-  int32_t* big = nullptr;      // top-down vertices shared by the whole grid
+  int32_t* queues = nullptr;   // 2 x NBINS queues of n entries: [set][bin][n]
+  int32_t* ulist = nullptr;    // bottom-up: ascending list of unvisited vertices
   BfsCtl* ctl = nullptr;
 };
 
@@ -79,16 +85,15 @@ struct gt_graph {
   int32_t* deg = nullptr;       // cleaned degree per vertex
   uint8_t* vtype = nullptr;     // Alg. 8 classes
   int32_t* up = nullptr;        // edge-tree vertex -> the neighbour it hangs from (-1 top / none)
-  int32_t* vinfo = nullptr;     // >= 0 core id; <= -2: tree vertex whose up is core id (-2 - x); -1 other
+  int32_t* vinfo = nullptr;     // >= 0 core id; -2 - x: tree vertex hanging from core id x;
+                                // INT32_MIN: tree vertex hanging from a tree vertex; -1 other
   int32_t* new2old = nullptr;   // core id -> vertex id
   int32_t* old2core = nullptr;  // vertex id -> core id or -1
-  int32_t* epoch = nullptr;     // root-path marks for the tree-up resolution pass
   int32_t* resolve_list = nullptr;  // tree vertices whose up is a tree vertex, by height desc
   int32_t* resolve_up = nullptr;
   int64_t* resolve_ptr_host = nullptr;  // segment starts per height (host copy), nheights + 1
   int32_t resolve_heights = 0;
   int64_t resolve_n = 0;
-  int32_t cur_epoch = 0;
   gt::View core;   // core CSR + traversal state
   gt::View plain;  // full CSR + traversal state (keep_plain)
   int32_t* scratch_out = nullptr;  // device staging when the caller passes host outputs
@@ -99,6 +104,11 @@ struct gt_graph {
   // step timing (time_kernels): one event pair per level, host copy of the durations
   std::vector<cudaEvent_t> step_events;
   std::vector<double> step_ms;
+  // batched traversal: per-slot device storage (7 buffers per slot) and the slot table
+  std::vector<void*> batch_mem;
+  int batch_slots_alloc = 0;
+  void* batch_dev = nullptr;
+  int batch_dev_cap = 0;
   int64_t device_bytes = 0;
 };
 
@@ -129,5 +139,13 @@ int radix_sort_u64(uint64_t** keys, uint64_t** alt, int64_t nkeys, int bits, int
 
 // bfs.cu
 int run_bfs(gt_graph* g, View& v, bool et, int64_t root, int32_t* parent, int32_t* level, cudaStream_t s);
+
+// batch.cu
+int run_batch(gt_graph* const* graphs, int ngraphs, const int64_t* roots, const int32_t* roots_per_graph,
+              int32_t* const* parent, int32_t* const* level, cudaStream_t s);
+void free_batch_mem(gt_graph* g);
+
+// tune.cu
+int autotune(gt_graph* g, int nsample, uint64_t seed, cudaStream_t s, gt_tuning* out);
 
 }  // namespace gt

@@ -1,0 +1,132 @@
+"""Batched BFS (64-root lane words, one persistent launch) through the C-ABI: every row
+must equal the single-root answer bit for bit (checked against the CPU oracle)."""
+import numpy as np
+import pytest
+
+import graphgen
+import paper_2009_07463_gb300 as gt
+from helpers import oracle_many
+from oracle import OracleGraph
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available()
+    return t
+
+
+def run_batch(torch, graphs, roots):
+    outs_p, outs_l = [], []
+    for g, r in zip(graphs, roots):
+        outs_p.append(torch.full((max(len(r), 1), g.n), -7, dtype=torch.int32, device="cuda"))
+        outs_l.append(torch.full((max(len(r), 1), g.n), -7, dtype=torch.int32, device="cuda"))
+    gt.gt_bfs_batch(graphs, roots, outs_p, outs_l)
+    torch.cuda.synchronize()
+    return [p.cpu().numpy() for p in outs_p], [l.cpu().numpy() for l in outs_l]
+
+
+def check_rows(P, L, og, roots, what):
+    want = oracle_many(og, roots)
+    for i, (r, (wl, wp)) in enumerate(zip(roots, want)):
+        if not np.array_equal(L[i], wl):
+            bad = np.flatnonzero(L[i] != wl)[:8]
+            raise AssertionError(f"{what} root {r}: level differs at {bad.tolist()}: {L[i][bad]} vs {wl[bad]}")
+        if not np.array_equal(P[i], wp):
+            bad = np.flatnonzero(P[i] != wp)[:8]
+            raise AssertionError(f"{what} root {r}: parent differs at {bad.tolist()}: {P[i][bad]} vs {wp[bad]}")
+
+
+def test_batch_one_word_scale16(torch):
+    n = 1 << 16
+    e = graphgen.rmat_edges(16, 16, seed=1)
+    og = OracleGraph(e, n)
+    g = gt.gt_graph_build(e, n)
+    roots = graphgen.pick_roots(2, n, 64, og.degree()).tolist()
+    (P,), (L,) = run_batch(torch, [g], [roots])
+    check_rows(P, L, og, roots, "s16 batch")
+
+
+def test_batch_partial_second_word_and_duplicates(torch):
+    n = 1 << 14
+    e = graphgen.rmat_edges(14, 16, seed=3)
+    og = OracleGraph(e, n)
+    g = gt.gt_graph_build(e, n)
+    roots = graphgen.pick_roots(4, n, 90, og.degree()).tolist()
+    roots += roots[:7]  # the same root in several lanes
+    (P,), (L,) = run_batch(torch, [g], [roots])
+    check_rows(P, L, og, roots, "s14 97 roots")
+
+
+@pytest.mark.parametrize("mh", [0, 1, -1])
+def test_batch_every_root_class(torch, mh):
+    n = 1 << 13
+    e = graphgen.rmat_edges(13, 8, seed=11)
+    og = OracleGraph(e, n)
+    g = gt.gt_graph_build(e, n, mh=mh)
+    vt = g.vertex_type()
+    rng = np.random.default_rng(5)
+    roots = []
+    for cls in range(5):
+        ids = np.flatnonzero(vt == cls)
+        if ids.size:
+            roots += rng.choice(ids, size=min(15, ids.size), replace=False).tolist()
+    (P,), (L,) = run_batch(torch, [g], [roots])
+    check_rows(P, L, og, roots, f"mh={mh}")
+
+
+def test_batch_mixed_graphs(torch):
+    specs = [("rmat", 10, None), ("rmat", 12, None), ("uniform", 20000, 16), ("rmat", 15, None), ("rmat", 11, None)]
+    graphs, oracles, roots = [], [], []
+    for i, (kind, a, d) in enumerate(specs):
+        if kind == "rmat":
+            n = 1 << a
+            e = graphgen.rmat_edges(a, 16, seed=30 + i)
+        else:
+            n = a
+            e = graphgen.uniform_edges(n, n * d // 2, seed=30 + i)
+        og = OracleGraph(e, n)
+        graphs.append(gt.gt_graph_build(e, n))
+        oracles.append(og)
+        k = [64, 20, 64, 130, 0][i]
+        roots.append(graphgen.pick_roots(40 + i, n, k, og.degree()).tolist() if k else [])
+    P, L = run_batch(torch, graphs, roots)
+    for i, og in enumerate(oracles):
+        if roots[i]:
+            check_rows(P[i], L[i], og, roots[i], f"mixed graph {i}")
+
+
+HAND = {
+    "k2_and_isolated": ([(2, 3), (5, 6), (6, 5)], 8),
+    "spider": ([(0, 1), (1, 2), (0, 3), (3, 4), (0, 5), (5, 6), (6, 7)], 8),
+    "path": ([(i, i + 1) for i in range(20)], 21),
+    "lollipop": ([(i, (i + 1) % 6) for i in range(6)] + [(5, 6), (6, 7), (7, 8), (8, 9), (7, 10)], 11),
+}
+
+
+@pytest.mark.parametrize("mh", [0, 2, -1])
+def test_batch_hand_graphs_all_roots(torch, mh):
+    graphs, oracles, roots = [], [], []
+    for name, (pairs, n) in sorted(HAND.items()):
+        e = np.array(pairs, dtype=np.int64)
+        oracles.append(OracleGraph(e, n))
+        graphs.append(gt.gt_graph_build(e, n, mh=mh))
+        roots.append(list(range(n)))
+    P, L = run_batch(torch, graphs, roots)
+    for i, og in enumerate(oracles):
+        check_rows(P[i], L[i], og, roots[i], f"hand {i} mh={mh}")
+
+
+def test_batch_equals_single_calls_and_repeats(torch):
+    n = 1 << 15
+    e = graphgen.rmat_edges(15, 16, seed=8)
+    g = gt.gt_graph_build(e, n)
+    deg = g.degree()
+    roots = graphgen.pick_roots(9, n, 64, deg).tolist()
+    for rep in range(2):  # second call reuses the slot storage
+        (P,), (L,) = run_batch(torch, [g], [roots])
+        for i, r in enumerate(roots[:16]):
+            p, l = g.bfs(r)
+            assert np.array_equal(L[i], l) and np.array_equal(P[i], p), f"rep {rep} root {r}"

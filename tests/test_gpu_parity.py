@@ -161,9 +161,9 @@ def test_direction_and_launch_mode_independence(torch_cuda):
     want = oracle_many(og, roots)
     for force in (0, 1, 2):
         for mode in (0, 1):
-            for thr in ((32, 4096, 8), (1, 2, 0), (8, 64, 1000)):
-                g.set_tuning(force_direction=force, launch_mode=mode, td_warp_min=thr[0], td_grid_min=thr[1],
-                             bu_thread_scan=thr[2], blocks_per_sm=1 + force)
+            for thr in ((32, 1024, 32768, 8), (1, 2, 3, 0), (8, 16, 64, 1000), (4, 1 << 20, 1 << 30, 2)):
+                g.set_tuning(force_direction=force, launch_mode=mode, td_warp_min=thr[0], td_cta_min=thr[1],
+                             td_grid_min=thr[2], bu_thread_scan=thr[3], blocks_per_sm=1 + force)
                 for r, w in zip(roots.tolist(), want):
                     what = f"force={force} mode={mode} thr={thr} root {r}"
                     assert_same(bfs_dev(torch, g, r), w, what)
