@@ -382,7 +382,13 @@ def main():
         for r in roots:
             g.bfs(r, parent, level, stream=stream)
             timed.append(g.trace())
-        g.set_tuning(count_work=0, launch_mode=1 if a.launch_mode == "host" else 0, time_kernels=0)
+        g.set_tuning(count_work=0, launch_mode=1 if a.launch_mode == "host" else 0, time_kernels=1)
+        phases = []
+        for r in roots:
+            g.bfs(r, parent, level, stream=stream)
+            phases.append(g.timing())
+        g.set_tuning(time_kernels=0)
+        out["phases_ms_mean"] = {k: round(sum(p[k] for p in phases) / len(phases), 4) for k in phases[0]}
         nc = st["n_core"]
         nwords = -(-max(nc, 1) // 32)
         nwords = -(-nwords // 128) * 128
@@ -420,7 +426,7 @@ def main():
                                   "CUDA events around each launch (host-driven kernel-timing pass, same roots)"}
         if a.trace_out:
             json.dump({"roots": roots, "counted": counted, "timed": timed, "tuples": tuples,
-                       "run_ms": run_ms}, open(a.trace_out, "w"))
+                       "run_ms": run_ms, "phases": phases}, open(a.trace_out, "w"))
 
     if oracle is not None:
         out["cpu_baseline"] = cpu_baseline_obj(oracle_result(*oracle, timeout=1800), a.cpu_roots)

@@ -61,8 +61,8 @@ typedef struct gt_config {
 
 /* Run-time tuning of the traversal; results never depend on it. */
 typedef struct gt_tuning {
-  int32_t alpha;        /* top-down -> bottom-up when m_f * alpha > m_u (default 14) */
-  int32_t beta;         /* bottom-up -> top-down when n_f * beta < n and shrinking (24) */
+  int32_t alpha;        /* top-down -> bottom-up when m_f * alpha > m_u (default 64) */
+  int32_t beta;         /* bottom-up -> top-down when n_f * beta < n and shrinking (256) */
   int32_t td_warp_min;  /* top-down: degree above which a whole warp takes a vertex (32) */
   int32_t td_cta_min;   /* top-down: degree above which a whole CTA takes a vertex (256) */
   int32_t td_grid_min;  /* top-down: degree above which the vertex's edges join one flat
@@ -74,8 +74,9 @@ typedef struct gt_tuning {
   int32_t launch_mode;  /* 0 = whole level loop in one CUDA graph with device-side
                            control (default), 1 = host-driven loop (one readback per level) */
   int32_t count_work;   /* 1: count examined edges per level (slower; for the trace) */
-  int32_t time_kernels; /* 1 (with launch_mode = 1): time each level's step kernels with
-                           CUDA events on the caller's stream; reported in the trace */
+  int32_t time_kernels; /* 1: time the phases of each traversal (gt_bfs_timing) and, with
+                           launch_mode = 1, each level's step kernels (gt_bfs_trace), with
+                           CUDA events on the caller's stream; each call then synchronises */
   int32_t batch_alpha;  /* gt_bfs_batch: lane word goes bottom-up when the next frontier's
                            summed degree * batch_alpha > core edges (default 14) */
   int32_t batch_beta;   /* gt_bfs_batch: back to top-down when frontier * batch_beta < core
@@ -157,6 +158,12 @@ GT_API int gt_bfs_batch(const gt_graph_t* graphs, int32_t ngraphs, const int64_t
  * keeps the fastest in the handle (also copied to *best if non-null). Results do not
  * depend on the setting. Synchronises `stream`; allocates temporary device buffers. */
 GT_API int gt_autotune(gt_graph_t g, int32_t nsample, uint64_t seed, gt_tuning* best, void* stream);
+/* Phase times of the last traversal run with time_kernels = 1: start (state reset, root
+ * walk), the level loop, and the output pass (tree resolution and scatter); -1 if none. */
+typedef struct gt_bfs_timing_t {
+  double start_ms, loop_ms, output_ms;
+} gt_bfs_timing_t;
+GT_API int gt_bfs_timing(gt_graph_t g, gt_bfs_timing_t* out);
 /* Per-level trace of the last gt_bfs / gt_bfs_plain on g (synchronises the stream it
  * ran on). Writes up to cap entries, *nlevels = levels run. */
 GT_API int gt_bfs_trace(gt_graph_t g, gt_level_info* out, int32_t cap, int32_t* nlevels);
@@ -166,6 +173,51 @@ GT_API int gt_bfs_trace(gt_graph_t g, gt_level_info* out, int32_t cap, int32_t* 
  * GT_EINVAL if a tuple holds an id outside [0, n) (nothing is read out of bounds). */
 GT_API int gt_count_traversed(const int64_t* edges, int64_t m, const int32_t* level, int64_t n, int64_t* out,
                               void* stream);
+
+/* ---- Serving: continuous batching over resident graphs (no counterpart in the paper) ----
+ * A server keeps graph handles resident, queues single-root queries per graph, and a
+ * scheduler thread turns the pending roots of a graph into batched launches (64 roots per
+ * lane word, as gt_bfs_batch) whenever one of its streams is free: at once when the GPU
+ * is idle, otherwise after up to window_us to fill lane words. Queries that arrive while
+ * batches run join the next batch, which runs beside those in flight (each stream's
+ * launch takes 1/streams of the SMs). Each result equals gt_bfs from that root. */
+typedef struct gt_serve_config {
+  int64_t hbm_budget_bytes; /* graphs + batch storage admitted up to this (default 48 GiB) */
+  int32_t streams;          /* batches in flight at once (default 2) */
+  int32_t max_batch_roots;  /* roots per launch (default 256) */
+  double window_us;         /* wait to fill lane words while other batches run (default 200) */
+} gt_serve_config;
+
+typedef struct gt_serve_stats {
+  int64_t submitted, completed, failed, batches, inflight, pending;
+  double p50_us, p99_us, mean_us, max_us; /* submit -> results in the caller's buffers */
+  double qps;                             /* completed / (last completion - first submit) */
+  int64_t device_bytes;                   /* graphs + batch storage held against the budget */
+} gt_serve_stats;
+
+typedef struct gt_server* gt_server_t;
+
+GT_API void gt_serve_config_default(gt_serve_config* cfg);
+/* Starts a server (and its scheduler thread) on the current device. cfg may be NULL. */
+GT_API int gt_serve_create(const gt_serve_config* cfg, gt_server_t* out);
+/* Makes a built graph resident for queries; GT_ENOMEM if its device memory plus one lane
+ * word of batch storage would exceed the budget. The server does not own the handle,
+ * which must outlive the server and must not be freed while queries are pending. */
+GT_API int gt_serve_add_graph(gt_server_t s, gt_graph_t g, int32_t* gid);
+/* Queues a BFS from `root` on graph gid. parent and level are caller-owned device
+ * int32[n] buffers that receive the result; they must stay valid until gt_serve_poll
+ * reports completion. Thread-safe. */
+GT_API int gt_serve_submit(gt_server_t s, int32_t gid, int64_t root, int32_t* parent, int32_t* level,
+                           uint64_t* ticket);
+/* Waits up to timeout_ms for the query: 0 when its results are in the buffers (the ticket
+ * is then released), GT_ETIMEOUT if not yet done (the ticket stays valid), another status
+ * if it failed (GT_EBUSY: the server was stopped before it ran). */
+GT_API int gt_serve_poll(gt_server_t s, uint64_t ticket, int32_t timeout_ms);
+GT_API int gt_serve_get_stats(gt_server_t s, gt_serve_stats* out);
+GT_API int gt_serve_reset_stats(gt_server_t s);
+/* Stops admitting, finishes the batches in flight, fails queries never dispatched, and
+ * frees the server (not the graphs). */
+GT_API int gt_serve_destroy(gt_server_t s);
 
 GT_API const char* gt_strerror(int code);
 GT_API const char* gt_last_error(void);

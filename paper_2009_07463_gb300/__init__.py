@@ -41,6 +41,17 @@ class gt_level_info(ctypes.Structure):
                 ("discovered", ctypes.c_int64), ("examined", ctypes.c_int64), ("step_ms", ctypes.c_double)]
 
 
+class gt_serve_config(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("streams", ctypes.c_int32), ("max_batch_roots", ctypes.c_int32),
+                ("window_us", ctypes.c_double)]
+
+
+class gt_serve_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "failed", "batches", "inflight", "pending")] + \
+               [(n, ctypes.c_double) for n in ("p50_us", "p99_us", "mean_us", "max_us", "qps")] + \
+               [("device_bytes", ctypes.c_int64)]
+
+
 class GtError(RuntimeError):
     def __init__(self, code: int, where: str, detail: str):
         super().__init__(f"{where}: {detail or 'error'} (status {code})")
@@ -72,8 +83,17 @@ def lib():
                 "gt_bfs": (ctypes.c_int, [p, i64, p, p, p]),
                 "gt_bfs_plain": (ctypes.c_int, [p, i64, p, p, p]),
                 "gt_bfs_trace": (ctypes.c_int, [p, p, i32, p]),
+                "gt_bfs_timing": (ctypes.c_int, [p, p]),
                 "gt_bfs_batch": (ctypes.c_int, [p, i32, p, p, p, p, p]),
                 "gt_autotune": (ctypes.c_int, [p, i32, ctypes.c_uint64, p, p]),
+                "gt_serve_config_default": (None, [p]),
+                "gt_serve_create": (ctypes.c_int, [p, p]),
+                "gt_serve_add_graph": (ctypes.c_int, [p, p, p]),
+                "gt_serve_submit": (ctypes.c_int, [p, i32, i64, p, p, p]),
+                "gt_serve_poll": (ctypes.c_int, [p, ctypes.c_uint64, i32]),
+                "gt_serve_get_stats": (ctypes.c_int, [p, p]),
+                "gt_serve_reset_stats": (ctypes.c_int, [p]),
+                "gt_serve_destroy": (ctypes.c_int, [p]),
                 "gt_count_traversed": (ctypes.c_int, [p, i64, p, i64, p, p]),
                 "gt_strerror": (ctypes.c_char_p, [ctypes.c_int]),
                 "gt_last_error": (ctypes.c_char_p, []),
@@ -198,6 +218,12 @@ class Graph:
         _check(lib().gt_autotune(self._h, int(nsample), int(seed), ctypes.byref(t), _stream(stream)), "gt_autotune")
         return t
 
+    def timing(self) -> dict:
+        """Phase times (ms) of the last traversal run with time_kernels = 1."""
+        t = (ctypes.c_double * 3)()
+        _check(lib().gt_bfs_timing(self._h, t), "gt_bfs_timing")
+        return {"start_ms": t[0], "loop_ms": t[1], "output_ms": t[2]}
+
     def trace(self) -> list[dict]:
         cap = 4096
         arr = (gt_level_info * cap)()
@@ -274,6 +300,65 @@ def gt_bfs_batch(graphs, roots_per_graph, parents, levels, stream=None) -> None:
     pp = (ctypes.c_void_p * ng)(*[_ptr(x) for x in parents])
     lp = (ctypes.c_void_p * ng)(*[_ptr(x) for x in levels])
     _check(lib().gt_bfs_batch(hs, ng, ra, counts, pp, lp, _stream(stream)), "gt_bfs_batch")
+
+
+class Server:
+    """Continuous-batching BFS server over resident graphs (gt_serve_*)."""
+
+    def __init__(self, hbm_budget_bytes: int | None = None, streams: int | None = None,
+                 max_batch_roots: int | None = None, window_us: float | None = None):
+        cfg = gt_serve_config()
+        lib().gt_serve_config_default(ctypes.byref(cfg))
+        if hbm_budget_bytes is not None:
+            cfg.hbm_budget_bytes = int(hbm_budget_bytes)
+        if streams is not None:
+            cfg.streams = int(streams)
+        if max_batch_roots is not None:
+            cfg.max_batch_roots = int(max_batch_roots)
+        if window_us is not None:
+            cfg.window_us = float(window_us)
+        h = ctypes.c_void_p()
+        _check(lib().gt_serve_create(ctypes.byref(cfg), ctypes.byref(h)), "gt_serve_create")
+        self._h = h.value
+        self._graphs = []
+
+    def add_graph(self, g: Graph) -> int:
+        gid = ctypes.c_int32(0)
+        _check(lib().gt_serve_add_graph(self._h, g.handle, ctypes.byref(gid)), "gt_serve_add_graph")
+        self._graphs.append(g)  # keep the handle alive while the server holds it
+        return gid.value
+
+    def submit(self, gid: int, root: int, parent, level) -> int:
+        t = ctypes.c_uint64(0)
+        _check(lib().gt_serve_submit(self._h, int(gid), int(root), _ptr(parent), _ptr(level), ctypes.byref(t)),
+               "gt_serve_submit")
+        return t.value
+
+    def poll(self, ticket: int, timeout_ms: int = 10000) -> int:
+        """0 when done; GT_ETIMEOUT if not yet; raises on failure."""
+        rc = lib().gt_serve_poll(self._h, int(ticket), int(timeout_ms))
+        if rc not in (GT_OK, GT_ETIMEOUT):
+            _check(rc, "gt_serve_poll")
+        return rc
+
+    def stats(self) -> dict:
+        st = gt_serve_stats()
+        _check(lib().gt_serve_get_stats(self._h, ctypes.byref(st)), "gt_serve_get_stats")
+        return {k: getattr(st, k) for k, _ in gt_serve_stats._fields_}
+
+    def reset_stats(self):
+        _check(lib().gt_serve_reset_stats(self._h), "gt_serve_reset_stats")
+
+    def destroy(self):
+        if self._h:
+            lib().gt_serve_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 def gt_count_traversed(edges, level, stream=None, m: int | None = None) -> int:

@@ -21,6 +21,8 @@
 //
 // Every wait at a grid barrier is bounded; on timeout the kernel raises an error flag
 // and all CTAs return, and the call reports GT_ETIMEOUT.
+#include <string.h>
+
 #include <algorithm>
 #include <vector>
 
@@ -56,9 +58,9 @@ struct SlotDev {
   int32_t* P;   // [nc][64] parent vertex ids
   uint16_t* L;  // [nc][64] iteration at which the lane reached the vertex
   int32_t* fl[2];
-  // outputs: lane l of this slot writes rows out + l * n
-  int32_t* out_parent;
-  int32_t* out_level;
+  // outputs: lane l writes parent / level arrays outp[l] / outl[l] (n entries each)
+  int32_t* outp[64];
+  int32_t* outl[64];
   int32_t nlanes;
   int32_t alpha, beta;
   int32_t pad;
@@ -403,8 +405,8 @@ __global__ void __launch_bounds__(BT) batch_output(SlotDev* slots, int nslots) {
           pa = add ? fixed_parent : s.P[(int64_t)cid * 64 + l];
         }
         if (in) {
-          s.out_level[(int64_t)l * s.n + v] = lv;
-          s.out_parent[(int64_t)l * s.n + v] = pa;
+          s.outl[l][v] = lv;
+          s.outp[l][v] = pa;
         }
       }
     }
@@ -422,8 +424,8 @@ __global__ void batch_fixup(SlotDev* slots, int nslots) {
   if (l >= s.nlanes) return;
   const int32_t root = s.lane[l].root;
   if (s.vinfo[root] >= 0) return;
-  int32_t* lv = s.out_level + (int64_t)l * s.n;
-  int32_t* pa = s.out_parent + (int64_t)l * s.n;
+  int32_t* lv = s.outl[l];
+  int32_t* pa = s.outp[l];
   lv[root] = 0;
   pa[root] = root;
   int32_t v = root, k = 0;
@@ -459,8 +461,8 @@ __global__ void batch_resolve(SlotDev* slots, const ResolveSeg* segs, int nslots
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int l = (int)(t / len);
     const int64_t i = sg.b + t % len;
-    int32_t* lv = s.out_level + (int64_t)l * s.n;
-    int32_t* pa = s.out_parent + (int64_t)l * s.n;
+    int32_t* lv = s.outl[l];
+    int32_t* pa = s.outp[l];
     const int32_t v = sg.list[i];
     if (lv[v] != -2) continue;
     const int32_t u = sg.lup[i];
@@ -507,22 +509,15 @@ __global__ void batch_lanes(SlotDev* slots, int nslots) {
 
 }  // namespace
 
-// Device storage of one slot on a graph (core-sized), kept in the handle between calls.
-struct BatchSlotMem {
-  uint64_t* visit = nullptr;
-  uint64_t* front[2] = {nullptr, nullptr};
-  int32_t* P = nullptr;
-  uint16_t* L = nullptr;
-  int32_t* fl[2] = {nullptr, nullptr};
-};
-
 void free_batch_mem(gt_graph* g) {
   for (void* p : g->batch_mem) cudaFree(p);
   g->batch_mem.clear();
   g->batch_slots_alloc = 0;
 }
 
-static int ensure_slots(gt_graph* g, int need) {
+// Grows the handle's pool of lane-word storage (7 buffers per 64 roots, core-sized) to
+// `need` slots.
+int ensure_slots(gt_graph* g, int need) {
   const int64_t nc = std::max<int64_t>(g->core.n, 1);
   while (g->batch_slots_alloc < need) {
     void* p[7];
@@ -541,137 +536,192 @@ static int ensure_slots(gt_graph* g, int need) {
   return GT_OK;
 }
 
-int run_batch(gt_graph* const* graphs, int ngraphs, const int64_t* roots, const int32_t* rpg,
-              int32_t* const* parent, int32_t* const* level, cudaStream_t st) {
-  std::vector<SlotDev> hs;
-  std::vector<int> slot_graph;
-  int64_t ro = 0;
-  for (int gi = 0; gi < ngraphs; ++gi) {
-    gt_graph* g = graphs[gi];
-    const int r = rpg[gi];
-    const int ns = (r + 63) / 64;
-    int rc = ensure_slots(g, ns);
-    if (rc) return rc;
-    for (int k = 0; k < ns; ++k) {
-      SlotDev s{};
-      s.n = g->n;
-      s.nc = g->core.n;
-      s.nnz_core = g->core.nnz;
-      s.crow = g->core.row;
-      s.ccol = g->core.col;
-      s.vinfo = g->vinfo;
-      s.new2old = g->new2old;
-      s.up = g->up;
-      s.old2core = g->old2core;
-      void* const* m = &g->batch_mem[7 * k];
-      s.visit = (uint64_t*)m[0];
-      s.front[0] = (uint64_t*)m[1];
-      s.front[1] = (uint64_t*)m[2];
-      s.P = (int32_t*)m[3];
-      s.L = (uint16_t*)m[4];
-      s.fl[0] = (int32_t*)m[5];
-      s.fl[1] = (int32_t*)m[6];
-      s.nlanes = std::min(64, r - 64 * k);
-      s.out_parent = parent[gi] + (int64_t)64 * k * g->n;
-      s.out_level = level[gi] + (int64_t)64 * k * g->n;
-      s.alpha = g->tuning.batch_alpha;
-      s.beta = g->tuning.batch_beta;
-      s.active = 0;
-      for (int l = 0; l < s.nlanes; ++l) {
-        const int64_t root = roots[ro + 64 * k + l];
-        if (root < 0 || root >= g->n) {
-          set_error("gt_bfs_batch: root outside [0, n)");
-          return GT_EINVAL;
-        }
-        s.lane[l].root = (int32_t)root;
-        s.lane[l].start = -1;
-      }
-      hs.push_back(s);
-      slot_graph.push_back(gi);
-      const size_t nc = (size_t)std::max<int64_t>(g->core.n, 1);
-      cudaMemsetAsync(s.visit, 0, 8 * nc, st);
-      cudaMemsetAsync(s.front[0], 0, 8 * nc, st);
-      cudaMemsetAsync(s.front[1], 0, 8 * nc, st);
-    }
-    ro += r;
-  }
-  const int ns = (int)hs.size();
-  if (ns == 0) return GT_OK;
-  if (ns > MAX_SLOTS_SMEM) {
-    set_error("gt_bfs_batch: more than 256 lane words (16384 roots) in one call");
+size_t slot_bytes(const gt_graph* g) { return (size_t)std::max<int64_t>(g->core.n, 1) * (8 * 3 + 256 + 128 + 8); }
+
+void batch_ctx_free(BatchCtx* c) {
+  if (!c) return;
+  if (c->dev) cudaFree(c->dev);
+  if (c->seg_dev) cudaFree(c->seg_dev);
+  if (c->h_err) cudaFreeHost(c->h_err);
+  c->dev = nullptr;
+  c->seg_dev = nullptr;
+  c->h_err = nullptr;
+  c->cap = 0;
+  c->seg_cap = 0;
+}
+
+int batch_launch(BatchCtx* ctx, const SlotSpec* specs, int nspecs, int sm_share, cudaStream_t st) {
+  if (nspecs <= 0) return GT_OK;
+  if (nspecs > MAX_SLOTS_SMEM) {
+    set_error("batched BFS: more than 256 lane words (16384 roots) in one launch");
     return GT_EINVAL;
   }
-  gt_graph* g0 = graphs[0];
-  if (!g0->batch_dev || g0->batch_dev_cap < ns) {
-    if (g0->batch_dev) cudaFree(g0->batch_dev);
-    g0->batch_dev = nullptr;
-    const size_t bytes = sizeof(SlotDev) * ns + sizeof(SlotCtl) * ns + sizeof(BatchCtl) + sizeof(ResolveSeg) * ns + 1024;
-    int rc = device_malloc(g0, &g0->batch_dev, bytes);
+  const int ns = nspecs;
+  const size_t t_slots = (sizeof(SlotDev) * ns + 255) & ~(size_t)255;
+  const size_t t_ctl = (sizeof(SlotCtl) * ns + 255) & ~(size_t)255;
+  const size_t bytes = t_slots + t_ctl + 256 + sizeof(ResolveSeg) * ns * 2 + 256;
+  if (ctx->cap < ns) {
+    if (ctx->dev) cudaFree(ctx->dev);
+    ctx->dev = nullptr;
+    int rc = cuda_fail(cudaMalloc(&ctx->dev, bytes), "batch table");
     if (rc) return rc;
-    g0->batch_dev_cap = ns;
+    ctx->cap = ns;
   }
-  char* base = (char*)g0->batch_dev;
+  if (!ctx->h_err) {
+    int rc = cuda_fail(cudaHostAlloc((void**)&ctx->h_err, sizeof(int) * 4, cudaHostAllocDefault), "pinned status");
+    if (rc) return rc;
+  }
+  ctx->h_err[0] = 0;
+  std::vector<SlotDev> hs(ns);
+  int maxh = 0;
+  gt_graph* g0 = specs[0].g;
+  for (int i = 0; i < ns; ++i) {
+    const SlotSpec& sp = specs[i];
+    gt_graph* g = sp.g;
+    SlotDev& d = hs[i];
+    memset(&d, 0, sizeof(d));
+    d.n = g->n;
+    d.nc = g->core.n;
+    d.nnz_core = g->core.nnz;
+    d.crow = g->core.row;
+    d.ccol = g->core.col;
+    d.vinfo = g->vinfo;
+    d.new2old = g->new2old;
+    d.up = g->up;
+    d.old2core = g->old2core;
+    d.visit = (uint64_t*)sp.mem[0];
+    d.front[0] = (uint64_t*)sp.mem[1];
+    d.front[1] = (uint64_t*)sp.mem[2];
+    d.P = (int32_t*)sp.mem[3];
+    d.L = (uint16_t*)sp.mem[4];
+    d.fl[0] = (int32_t*)sp.mem[5];
+    d.fl[1] = (int32_t*)sp.mem[6];
+    d.nlanes = sp.nlanes;
+    d.alpha = g->tuning.batch_alpha;
+    d.beta = g->tuning.batch_beta;
+    for (int l = 0; l < sp.nlanes; ++l) {
+      const int64_t root = sp.roots[l];
+      if (root < 0 || root >= g->n || !sp.outp[l] || !sp.outl[l]) {
+        set_error("batched BFS: root outside [0, n) or null output");
+        return GT_EINVAL;
+      }
+      d.lane[l].root = (int32_t)root;
+      d.lane[l].start = -1;
+      d.outp[l] = sp.outp[l];
+      d.outl[l] = sp.outl[l];
+    }
+    maxh = std::max(maxh, g->resolve_heights);
+    const size_t nc = (size_t)std::max<int64_t>(g->core.n, 1);
+    cudaMemsetAsync(d.visit, 0, 8 * nc, st);
+    cudaMemsetAsync(d.front[0], 0, 8 * nc, st);
+    cudaMemsetAsync(d.front[1], 0, 8 * nc, st);
+  }
+  char* base = (char*)ctx->dev;
   SlotDev* d_slots = (SlotDev*)base;
-  SlotCtl* d_ctl = (SlotCtl*)(base + ((sizeof(SlotDev) * ns + 255) & ~(size_t)255));
-  BatchCtl* d_bc = (BatchCtl*)((char*)d_ctl + ((sizeof(SlotCtl) * ns + 255) & ~(size_t)255));
-  ResolveSeg* d_seg = (ResolveSeg*)((char*)d_bc + 256);
+  SlotCtl* d_ctl = (SlotCtl*)(base + t_slots);
+  BatchCtl* d_bc = (BatchCtl*)(base + t_slots + t_ctl);
+  ResolveSeg* d_seg = (ResolveSeg*)(base + t_slots + t_ctl + 256);
   int rc = cuda_fail(cudaMemcpyAsync(d_slots, hs.data(), sizeof(SlotDev) * ns, cudaMemcpyHostToDevice, st), "slots");
   if (rc) return rc;
   std::vector<SlotCtl> hc(ns);
   for (int i = 0; i < ns; ++i) hc[i] = SlotCtl{{0, 0}, 0, 0, DIR_TD, 0, 0};
-  BatchCtl hb{0u, 0, ns, 0};
+  const BatchCtl hb{0u, 0, ns, 0};
   cudaMemcpyAsync(d_ctl, hc.data(), sizeof(SlotCtl) * ns, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(d_bc, &hb, sizeof(hb), cudaMemcpyHostToDevice, st);
   batch_lanes<<<ns, 64, 0, st>>>(d_slots, ns);
   batch_init<<<ns, 64, 0, st>>>(d_slots, d_ctl, ns);
-  // slots whose lanes all start nowhere are done before the loop
-  // (handled in the first decide: an empty frontier ends the slot)
-  int dev = g0->device, nb_per_sm = 0;
+  int nb_per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_per_sm, batch_run, BT, 0);
-  const int grid = std::max(1, std::min(nb_per_sm, 4)) * g0->launch.sms;
+  const int share = std::max(1, std::min(sm_share > 0 ? sm_share : g0->launch.sms, g0->launch.sms));
+  const int grid = std::max(1, std::min(nb_per_sm, 4)) * share;
   int32_t cl = 0;
-  void* kargs[] = {(void*)&d_slots, (void*)&d_ctl, (void*)&ns, (void*)&d_bc, (void*)&cl};
-  (void)dev;
+  int nsl = ns;
+  void* kargs[] = {(void*)&d_slots, (void*)&d_ctl, (void*)&nsl, (void*)&d_bc, (void*)&cl};
   rc = cuda_fail(cudaLaunchCooperativeKernel((void*)batch_run, dim3(grid), dim3(BT), kargs, 0, st), "batch launch");
   if (rc) return rc;
-  batch_output<<<g0->launch.sms * 16, BT, 0, st>>>(d_slots, ns);
+  batch_output<<<share * 16, BT, 0, st>>>(d_slots, ns);
   batch_fixup<<<ns, 64, 0, st>>>(d_slots, ns);
-  int maxh = 0;
-  for (int gi = 0; gi < ngraphs; ++gi) maxh = std::max(maxh, graphs[gi]->resolve_heights);
   if (maxh > 0) {
-    std::vector<ResolveSeg> segs(ns);
-    for (int h = 0; h < maxh; ++h) {
-      bool any = false;
+    // heights are processed top down; each slot walks its own graph's segments
+    std::vector<ResolveSeg> segs((size_t)ns * maxh);
+    for (int h = 0; h < maxh; ++h)
       for (int i = 0; i < ns; ++i) {
-        gt_graph* g = graphs[slot_graph[i]];
+        gt_graph* g = specs[i].g;
         ResolveSeg sg{g->resolve_list, g->resolve_up, 0, 0};
         if (h < g->resolve_heights) {
           sg.b = g->resolve_ptr_host[h];
           sg.e = g->resolve_ptr_host[h + 1];
-          any |= sg.e > sg.b;
         }
-        segs[i] = sg;
+        segs[(size_t)h * ns + i] = sg;
       }
-      if (!any) continue;
-      cudaMemcpyAsync(d_seg, segs.data(), sizeof(ResolveSeg) * ns, cudaMemcpyHostToDevice, st);
-      batch_resolve<<<dim3(64, ns), BT, 0, st>>>(d_slots, d_seg, ns);
+    if (ctx->seg_cap < (int64_t)segs.size()) {
+      if (ctx->seg_dev) cudaFree(ctx->seg_dev);
+      ctx->seg_dev = nullptr;
+      rc = cuda_fail(cudaMalloc(&ctx->seg_dev, sizeof(ResolveSeg) * segs.size()), "resolve table");
+      if (rc) return rc;
+      ctx->seg_cap = (int64_t)segs.size();
     }
+    ResolveSeg* dseg = (ResolveSeg*)ctx->seg_dev;
+    cudaMemcpyAsync(dseg, segs.data(), sizeof(ResolveSeg) * segs.size(), cudaMemcpyHostToDevice, st);
+    for (int h = 0; h < maxh; ++h) batch_resolve<<<dim3(64, ns), BT, 0, st>>>(d_slots, dseg + (size_t)h * ns, ns);
   }
-  rc = cuda_fail(cudaGetLastError(), "batch kernels");
-  if (rc) return rc;
-  int err = 0;
-  rc = cuda_fail(cudaMemcpyAsync(&err, &d_bc->err, sizeof(int), cudaMemcpyDeviceToHost, st), "batch status");
-  if (!rc) rc = cuda_fail(cudaStreamSynchronize(st), "batch sync");
-  if (rc) return rc;
+  (void)d_seg;
+  cudaMemcpyAsync(ctx->h_err, &d_bc->err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  return cuda_fail(cudaGetLastError(), "batch kernels");
+}
+
+int batch_status(const BatchCtx* ctx) {
+  const int err = ctx->h_err ? ctx->h_err[0] : 0;
   if (err == 1) {
-    set_error("gt_bfs_batch: a grid barrier wait ran out");
+    set_error("batched BFS: a grid barrier wait ran out");
     return GT_ETIMEOUT;
   }
   if (err == 2) {
-    set_error("gt_bfs_batch: traversal deeper than 65533 levels");
+    set_error("batched BFS: traversal deeper than 65533 levels");
     return GT_ENOTSUP;
   }
   return GT_OK;
+}
+
+int run_batch(gt_graph* const* graphs, int ngraphs, const int64_t* roots, const int32_t* rpg,
+              int32_t* const* parent, int32_t* const* level, cudaStream_t st) {
+  std::vector<SlotSpec> specs;
+  std::vector<int32_t*> lanes_p, lanes_l;
+  int64_t total_words = 0;
+  for (int gi = 0; gi < ngraphs; ++gi) total_words += (rpg[gi] + 63) / 64;
+  lanes_p.reserve((size_t)total_words * 64);
+  lanes_l.reserve((size_t)total_words * 64);
+  int64_t ro = 0;
+  for (int gi = 0; gi < ngraphs; ++gi) {
+    gt_graph* g = graphs[gi];
+    const int r = rpg[gi];
+    const int nsg = (r + 63) / 64;
+    int rc = ensure_slots(g, nsg);
+    if (rc) return rc;
+    for (int k = 0; k < nsg; ++k) {
+      SlotSpec sp;
+      sp.g = g;
+      sp.mem = &g->batch_mem[7 * k];
+      sp.nlanes = std::min(64, r - 64 * k);
+      sp.roots = roots + ro + 64 * k;
+      const size_t off = lanes_p.size();
+      for (int l = 0; l < sp.nlanes; ++l) {
+        lanes_p.push_back(parent[gi] + (int64_t)(64 * k + l) * g->n);
+        lanes_l.push_back(level[gi] + (int64_t)(64 * k + l) * g->n);
+      }
+      sp.outp = lanes_p.data() + off;
+      sp.outl = lanes_l.data() + off;
+      specs.push_back(sp);
+    }
+    ro += r;
+  }
+  if (specs.empty()) return GT_OK;
+  gt_graph* g0 = graphs[0];
+  if (!g0->batch_ctx) g0->batch_ctx = new BatchCtx();
+  int rc = batch_launch(g0->batch_ctx, specs.data(), (int)specs.size(), 0, st);
+  if (!rc) rc = cuda_fail(cudaStreamSynchronize(st), "batch sync");
+  if (!rc) rc = batch_status(g0->batch_ctx);
+  return rc;
 }
 
 }  // namespace gt

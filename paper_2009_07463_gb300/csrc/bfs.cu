@@ -160,7 +160,7 @@ constexpr int TD_WIN = 1024;  // bin-3 vertices whose edges one window flattens
 //  bin 2: a CTA per vertex;  bin 1: a warp per vertex;
 //  bin 0 (degree <= td_warp_min): a warp takes 32 vertices and its lanes share out their
 //    edges (lane-to-vertex by a search over the warp's prefix sum of degrees).
-__global__ void __launch_bounds__(BFS_THREADS) bfs_td(BfsArgs a) {
+__global__ void __launch_bounds__(BFS_THREADS, 4) bfs_td(BfsArgs a) {
   __shared__ int64_t s_pre[TD_WIN + 1];
   __shared__ int64_t s_beg[TD_WIN];
   __shared__ int32_t s_v[TD_WIN];
@@ -407,7 +407,7 @@ __device__ __forceinline__ bool visited_bit(const uint32_t* __restrict__ vc, int
 // (one atomic per distinct word); counts are committed once per CTA. The frontier
 // queue is not written here: the next bottom-up step reads the bitmap, and a top-down
 // step rebuilds the queue from the bitmaps first.
-__global__ void __launch_bounds__(BFS_THREADS) bfs_bu_scan(BfsArgs a) {
+__global__ void __launch_bounds__(BFS_THREADS, 4) bfs_bu_scan(BfsArgs a) {
   BfsCtl* ctl = a.ctl;
   const uint32_t* __restrict__ vc = ctl->vcur ? a.vis1 : a.vis0;
   uint32_t* vn = ctl->vcur ? a.vis0 : a.vis1;
@@ -434,26 +434,40 @@ __global__ void __launch_bounds__(BFS_THREADS) bfs_bu_scan(BfsArgs a) {
         e[j] = a.row[w[j] + 1];
       }
     }
-    int32_t u0[BU_V];
-#pragma unroll
-    for (int j = 0; j < BU_V; ++j) u0[j] = (s[j] < e[j]) ? a.col[s[j]] : -1;
+    // probe depth by depth: at every depth the open vertices of this lane issue their
+    // loads together, so BU_V dependent chains overlap
+    int64_t nx[BU_V];
 #pragma unroll
     for (int j = 0; j < BU_V; ++j) {
-      par[j] = (u0[j] >= 0 && visited_bit(vc, u0[j])) ? u0[j] : -1;
+      par[j] = -1;
+      nx[j] = s[j];
       lim[j] = min(e[j], s[j] + (int64_t)max(a.bu_scan, 1));
-      int64_t k = s[j] + 1;
-      if (par[j] < 0) {
-        for (; k < lim[j]; ++k) {
-          const int32_t u = a.col[k];
-          if (visited_bit(vc, u)) {
-            par[j] = u;
-            ++k;
-            break;
-          }
+    }
+    for (int r = 0; r < max(a.bu_scan, 1); ++r) {
+      int32_t u[BU_V];
+      bool any = false;
+#pragma unroll
+      for (int j = 0; j < BU_V; ++j) {
+        u[j] = -1;
+        if (par[j] < 0 && nx[j] < lim[j]) {
+          u[j] = a.col[nx[j]];
+          any = true;
         }
       }
-      examined += min(k, e[j]) - s[j];
+      if (!any) break;
+      uint32_t vw[BU_V];
+#pragma unroll
+      for (int j = 0; j < BU_V; ++j) vw[j] = u[j] >= 0 ? __ldg(&vc[u[j] >> 5]) : 0u;
+#pragma unroll
+      for (int j = 0; j < BU_V; ++j) {
+        if (u[j] >= 0) {
+          ++nx[j];
+          if ((vw[j] >> (u[j] & 31)) & 1u) par[j] = u[j];
+        }
+      }
     }
+#pragma unroll
+    for (int j = 0; j < BU_V; ++j) examined += nx[j] - s[j];
 #pragma unroll
     for (int j = 0; j < BU_V; ++j) {
       const bool fnd = par[j] >= 0;
@@ -669,26 +683,54 @@ __global__ void et_start(BfsArgs a, EtArgs e, int32_t root, int32_t alpha, int32
 // BFS state (parents back to vertex ids), edge-tree vertices hanging from a core vertex
 // from that vertex's level (Alg. 7 / Alg. 10 with levels), tree vertices hanging from a
 // tree vertex -2 ("resolve pending", see et_resolve), everything else -1.
+// Four consecutive vertices per thread: one 128-bit vinfo load, four independent state
+// gathers, four independent id gathers, 128-bit stores (when n and the outputs allow).
+__device__ __forceinline__ void et_decode(int32_t info, int32_t& cid, int32_t& add) {
+  cid = -1;
+  add = 0;
+  if (info >= 0) {
+    cid = info;
+  } else if (info != INT32_MIN && info <= -2) {
+    cid = -2 - info;
+    add = 1;
+  }
+}
+
 __global__ void et_output(EtArgs e, const uint64_t* __restrict__ state, int32_t* __restrict__ parent,
-                          int32_t* __restrict__ level) {
-  for (int64_t v = gtid(); v < e.n; v += gthreads()) {
-    const int32_t info = e.vinfo[v];
-    int32_t l = -1, p = -1;
-    if (info >= 0) {
-      const uint64_t s = state[info];
-      if (s != UNVISITED) {
-        l = (int32_t)(s >> 32);
-        p = e.new2old[(uint32_t)s];
+                          int32_t* __restrict__ level, int vec) {
+  const int64_t n4 = vec ? e.n / 4 : 0;
+  for (int64_t i = gtid(); i < n4; i += gthreads()) {
+    const int4 in = reinterpret_cast<const int4*>(e.vinfo)[i];
+    const int32_t info[4] = {in.x, in.y, in.z, in.w};
+    int32_t cid[4], add[4], l[4], p[4];
+    uint64_t st[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      et_decode(info[k], cid[k], add[k]);
+      st[k] = cid[k] >= 0 ? state[cid[k]] : UNVISITED;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      l[k] = info[k] == INT32_MIN ? -2 : -1;
+      p[k] = l[k];
+      if (st[k] != UNVISITED) {
+        l[k] = (int32_t)(st[k] >> 32) + add[k];
+        p[k] = e.new2old[add[k] ? cid[k] : (int32_t)(uint32_t)st[k]];
       }
-    } else if (info == INT32_MIN) {
-      l = -2;
-      p = -2;
-    } else if (info <= -2) {
-      const int32_t cu = -2 - info;
-      const uint64_t s = state[cu];
-      if (s != UNVISITED) {
-        l = (int32_t)(s >> 32) + 1;
-        p = e.new2old[cu];
+    }
+    reinterpret_cast<int4*>(level)[i] = make_int4(l[0], l[1], l[2], l[3]);
+    reinterpret_cast<int4*>(parent)[i] = make_int4(p[0], p[1], p[2], p[3]);
+  }
+  for (int64_t v = 4 * n4 + gtid(); v < e.n; v += gthreads()) {
+    const int32_t info = e.vinfo[v];
+    int32_t cid, add;
+    et_decode(info, cid, add);
+    int32_t l = info == INT32_MIN ? -2 : -1, p = l;
+    if (cid >= 0) {
+      const uint64_t st = state[cid];
+      if (st != UNVISITED) {
+        l = (int32_t)(st >> 32) + add;
+        p = e.new2old[add ? cid : (int32_t)(uint32_t)st];
       }
     }
     level[v] = l;
@@ -899,6 +941,10 @@ int run_level_loop(gt_graph* g, View& v, int which, cudaStream_t s) {
 int run_bfs(gt_graph* g, View& v, bool et, int64_t root, int32_t* parent, int32_t* level, cudaStream_t s) {
   const gt_tuning& t = g->tuning;
   const BfsArgs a = make_args(v, t);
+  const bool timed = t.time_kernels;
+  if (timed && !g->phase_events[0])
+    for (int i = 0; i < 4; ++i) cudaEventCreate(&g->phase_events[i]);
+  if (timed) cudaEventRecord(g->phase_events[0], s);
   const int gs = grid_stream(g, std::max<int64_t>(v.n, v.nwords));
   bfs_reset<<<gs, 256, 0, s>>>(v.state, v.vis[0], v.n, v.nwords);
   EtArgs e{g->vinfo, g->up, g->old2core, g->new2old, g->n};
@@ -908,11 +954,14 @@ int run_bfs(gt_graph* g, View& v, bool et, int64_t root, int32_t* parent, int32_
     bfs_start_plain<<<1, 1, 0, s>>>(a, (int32_t)root, t.alpha, t.beta, t.force_direction);
   int rc = cuda_fail(cudaGetLastError(), "bfs start");
   if (rc != GT_OK) return rc;
+  if (timed) cudaEventRecord(g->phase_events[1], s);
   rc = run_level_loop(g, v, et ? 0 : 1, s);
   if (rc != GT_OK) return rc;
+  if (timed) cudaEventRecord(g->phase_events[2], s);
   if (et) {
     const int go = grid_stream(g, g->n);
-    et_output<<<go, 256, 0, s>>>(e, v.state, parent, level);
+    const int vec = ((uintptr_t)parent % 16 == 0) && ((uintptr_t)level % 16 == 0);
+    et_output<<<go, 256, 0, s>>>(e, v.state, parent, level, vec);
     et_fixup<<<1, 1, 0, s>>>(e, (int32_t)root, parent, level);
     for (int h = 0; h < g->resolve_heights; ++h) {
       const int64_t b = g->resolve_ptr_host[h], en = g->resolve_ptr_host[h + 1];
@@ -924,7 +973,17 @@ int run_bfs(gt_graph* g, View& v, bool et, int64_t root, int32_t* parent, int32_
   }
   g->last_stream = s;
   g->last_ctl = v.ctl;
-  return cuda_fail(cudaGetLastError(), "bfs output");
+  rc = cuda_fail(cudaGetLastError(), "bfs output");
+  if (timed && rc == GT_OK) {
+    cudaEventRecord(g->phase_events[3], s);
+    rc = cuda_fail(cudaEventSynchronize(g->phase_events[3]), "timing sync");
+    for (int i = 0; i < 3 && rc == GT_OK; ++i) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, g->phase_events[i], g->phase_events[i + 1]);
+      g->phase_ms[i] = ms;
+    }
+  }
+  return rc;
 }
 
 }  // namespace gt

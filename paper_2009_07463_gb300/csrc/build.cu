@@ -365,6 +365,8 @@ void free_graph(gt_graph* g) {
   for (int i = 0; i < 2; ++i)
     if (g->loop_exec[i]) cudaGraphExecDestroy(g->loop_exec[i]);
   for (cudaEvent_t ev : g->step_events) cudaEventDestroy(ev);
+  for (cudaEvent_t& ev : g->phase_events)
+    if (ev) cudaEventDestroy(ev);
   g->step_events.clear();
   if (g->core.row != g->row) {
     cudaFree(g->core.row);
@@ -381,7 +383,11 @@ void free_graph(gt_graph* g) {
   cudaFree(g->new2old);
   cudaFree(g->old2core);
   free_batch_mem(g);
-  cudaFree(g->batch_dev);
+  if (g->batch_ctx) {
+    batch_ctx_free(g->batch_ctx);
+    delete g->batch_ctx;
+    g->batch_ctx = nullptr;
+  }
   cudaFree(g->resolve_list);
   cudaFree(g->resolve_up);
   cudaFree(g->scratch_out);

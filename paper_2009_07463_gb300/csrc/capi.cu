@@ -130,8 +130,8 @@ GT_API void gt_config_default(gt_config* c) {
 GT_API void gt_tuning_default(gt_tuning* t) {
   if (!t) return;
   memset(t, 0, sizeof(*t));
-  t->alpha = 14;
-  t->beta = 24;
+  t->alpha = 64;
+  t->beta = 256;
   t->td_warp_min = 32;
   t->td_cta_min = 256;
   t->td_grid_min = 2048;
@@ -223,7 +223,7 @@ GT_API int gt_graph_set_tuning(gt_graph_t g, const gt_tuning* t) {
       t->td_grid_min < t->td_cta_min ||
       t->bu_thread_scan < 0 || t->blocks_per_sm < 1 || t->blocks_per_sm > 32 || t->force_direction < 0 ||
       t->force_direction > 2 || t->launch_mode < 0 || t->launch_mode > 1 || t->time_kernels < 0 ||
-      t->time_kernels > 1 || (t->time_kernels && t->launch_mode != 1) || t->batch_alpha < 1 ||
+      t->time_kernels > 1 || t->batch_alpha < 1 ||
       t->batch_beta < 1) {
     set_error("gt_graph_set_tuning: value out of range");
     return GT_EINVAL;
@@ -286,6 +286,14 @@ GT_API int gt_autotune(gt_graph_t g, int32_t nsample, uint64_t seed, gt_tuning* 
   rc = autotune(g, nsample, seed, s, best);
   g->last_stream = s;
   return rc;
+}
+
+GT_API int gt_bfs_timing(gt_graph_t g, gt_bfs_timing_t* out) {
+  if (!g || !out) return GT_EINVAL;
+  out->start_ms = g->phase_ms[0];
+  out->loop_ms = g->phase_ms[1];
+  out->output_ms = g->phase_ms[2];
+  return GT_OK;
 }
 
 GT_API int gt_bfs_trace(gt_graph_t g, gt_level_info* out, int32_t cap, int32_t* nlevels) {

@@ -70,6 +70,16 @@ struct LaunchCfg {
   int grid = 608;
 };
 
+// A reusable launch context of the batched traversal: device slot table and a pinned
+// status word read back after the launch completes.
+struct BatchCtx {
+  void* dev = nullptr;
+  int cap = 0;
+  void* seg_dev = nullptr;
+  int64_t seg_cap = 0;
+  int* h_err = nullptr;
+};
+
 }  // namespace gt
 
 struct gt_graph {
@@ -104,11 +114,12 @@ struct gt_graph {
   // step timing (time_kernels): one event pair per level, host copy of the durations
   std::vector<cudaEvent_t> step_events;
   std::vector<double> step_ms;
+  cudaEvent_t phase_events[4] = {nullptr, nullptr, nullptr, nullptr};
+  double phase_ms[3] = {-1.0, -1.0, -1.0};  // start, level loop, output (time_kernels)
   // batched traversal: per-slot device storage (7 buffers per slot) and the slot table
   std::vector<void*> batch_mem;
   int batch_slots_alloc = 0;
-  void* batch_dev = nullptr;
-  int batch_dev_cap = 0;
+  gt::BatchCtx* batch_ctx = nullptr;
   int64_t device_bytes = 0;
 };
 
@@ -141,8 +152,24 @@ int radix_sort_u64(uint64_t** keys, uint64_t** alt, int64_t nkeys, int bits, int
 int run_bfs(gt_graph* g, View& v, bool et, int64_t root, int32_t* parent, int32_t* level, cudaStream_t s);
 
 // batch.cu
+// One lane word (up to 64 roots of one graph) of a batched launch.
+struct SlotSpec {
+  gt_graph* g;
+  void* const* mem;         // 7 slot buffers from the graph's pool (ensure_slots)
+  int nlanes;
+  const int64_t* roots;     // nlanes roots
+  int32_t* const* outp;     // nlanes parent arrays (device, n entries)
+  int32_t* const* outl;     // nlanes level arrays
+};
 int run_batch(gt_graph* const* graphs, int ngraphs, const int64_t* roots, const int32_t* roots_per_graph,
               int32_t* const* parent, int32_t* const* level, cudaStream_t s);
+int ensure_slots(gt_graph* g, int need);
+size_t slot_bytes(const gt_graph* g);
+// Enqueues a whole batched traversal on `st` (cooperative kernel on sm_share SMs' worth of
+// CTAs, 0 = all); batch_status() reads its outcome once the stream has passed it.
+int batch_launch(BatchCtx* ctx, const SlotSpec* specs, int nspecs, int sm_share, cudaStream_t st);
+int batch_status(const BatchCtx* ctx);
+void batch_ctx_free(BatchCtx* c);
 void free_batch_mem(gt_graph* g);
 
 // tune.cu

@@ -1,0 +1,434 @@
+// serve.cu -- continuous-batching BFS server over resident graphs.
+//
+// Queries (graph, root, caller-owned device outputs) are queued per graph. A scheduler
+// thread turns the pending roots of one graph into a batched launch (64 roots per lane
+// word, see batch.cu) whenever one of the server's streams is free: it dispatches at
+// once when the GPU is idle, otherwise it waits up to `window_us` to fill lane words.
+// Queries that arrive while batches are on the GPU join the next batch, which runs
+// beside the ones in flight (each stream's cooperative launch takes 1/streams of the
+// SMs), so their work overlaps on the device. Graphs are admitted against an HBM budget
+// (graph storage + one lane word of batch storage); more lane-word storage is taken
+// while the budget allows. Completion is signalled by a host callback on the stream,
+// which stamps every query's latency (submit -> results in the caller's buffers).
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "gt_internal.cuh"
+
+namespace gt {
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double now_us() {
+  return std::chrono::duration<double, std::micro>(Clock::now().time_since_epoch()).count();
+}
+
+struct Query {
+  uint64_t ticket = 0;
+  int32_t gid = 0;
+  int64_t root = 0;
+  int32_t* parent = nullptr;
+  int32_t* level = nullptr;
+  double t_submit = 0, t_done = 0;
+  bool done = false;
+  int rc = GT_OK;
+};
+
+struct SlotBuf {
+  void* p[7];
+};
+
+struct GraphEntry {
+  gt_graph* g = nullptr;
+  std::deque<Query*> pending;
+  std::vector<SlotBuf> slots;  // lane-word storage owned by the server
+  std::vector<int> free_slots;
+};
+
+struct Flight {
+  void* srv = nullptr;
+  int stream = 0;
+  int gid = 0;
+  std::vector<Query*> queries;
+  std::vector<int> slots;
+};
+
+}  // namespace
+}  // namespace gt
+
+struct gt_server {
+  gt_serve_config cfg{};
+  std::mutex mu;
+  std::condition_variable cv_sched, cv_done;
+  std::deque<gt::GraphEntry> graphs;  // stable addresses: the scheduler keeps references
+  std::unordered_map<uint64_t, gt::Query*> tickets;
+  uint64_t next_ticket = 1;
+  std::thread worker;
+  bool stop = false;
+  int device = 0;
+  int sms = 1;
+  std::vector<cudaStream_t> streams;
+  std::vector<gt::BatchCtx> ctxs;
+  std::vector<gt::Flight*> flights;  // per stream, null when free
+  int64_t used_bytes = 0;
+  // statistics
+  int64_t submitted = 0, completed = 0, failed = 0, batches = 0;
+  double t_first = 0, t_last = 0;
+  std::vector<double> lat_us;
+};
+
+namespace gt {
+namespace {
+
+void CUDART_CB on_flight_done(void* arg) {
+  Flight* f = (Flight*)arg;
+  gt_server* s = (gt_server*)f->srv;
+  const double t = now_us();
+  std::lock_guard<std::mutex> lk(s->mu);
+  const int rc = batch_status(&s->ctxs[f->stream]);
+  GraphEntry& ge = s->graphs[f->gid];
+  for (int k : f->slots) ge.free_slots.push_back(k);
+  for (Query* q : f->queries) {
+    q->done = true;
+    q->rc = rc;
+    q->t_done = t;
+    s->lat_us.push_back(t - q->t_submit);
+    if (rc) s->failed++;
+    s->completed++;
+  }
+  s->t_last = t;
+  s->flights[f->stream] = nullptr;
+  delete f;
+  s->cv_done.notify_all();
+  s->cv_sched.notify_all();
+}
+
+// Grows a graph's lane-word pool by one if the budget allows. Caller holds the lock.
+bool grow_slots(gt_server* s, GraphEntry& ge) {
+  const size_t sb = slot_bytes(ge.g);
+  if (s->used_bytes + (int64_t)sb > s->cfg.hbm_budget_bytes) return false;
+  const int64_t nc = std::max<int64_t>(ge.g->core.n, 1);
+  const size_t sz[7] = {8 * (size_t)nc, 8 * (size_t)nc, 8 * (size_t)nc, 256 * (size_t)nc, 128 * (size_t)nc,
+                        4 * (size_t)nc, 4 * (size_t)nc};
+  SlotBuf b{};
+  for (int i = 0; i < 7; ++i) {
+    if (cudaMalloc(&b.p[i], sz[i]) != cudaSuccess) {
+      cudaGetLastError();
+      for (int j = 0; j < i; ++j) cudaFree(b.p[j]);
+      return false;
+    }
+  }
+  ge.slots.push_back(b);
+  ge.free_slots.push_back((int)ge.slots.size() - 1);
+  s->used_bytes += (int64_t)sb;
+  return true;
+}
+
+// Picks the graph whose oldest pending query is oldest; -1 if none. Caller holds the lock.
+int oldest_graph(gt_server* s) {
+  int best = -1;
+  double t = 0;
+  for (size_t i = 0; i < s->graphs.size(); ++i) {
+    const GraphEntry& ge = s->graphs[i];
+    if (ge.pending.empty()) continue;
+    if (best < 0 || ge.pending.front()->t_submit < t) {
+      best = (int)i;
+      t = ge.pending.front()->t_submit;
+    }
+  }
+  return best;
+}
+
+void scheduler(gt_server* s) {
+  cudaSetDevice(s->device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  for (;;) {
+    int free_stream = -1, busy = 0;
+    for (size_t i = 0; i < s->flights.size(); ++i) {
+      if (s->flights[i]) ++busy;
+      else if (free_stream < 0) free_stream = (int)i;
+    }
+    if (s->stop && busy == 0) break;
+    const int gi = oldest_graph(s);
+    if (s->stop || gi < 0 || free_stream < 0) {
+      s->cv_sched.wait_for(lk, std::chrono::microseconds(200));
+      if (s->stop) {
+        // drop queries never dispatched
+        for (GraphEntry& ge : s->graphs)
+          while (!ge.pending.empty()) {
+            Query* q = ge.pending.front();
+            ge.pending.pop_front();
+            q->done = true;
+            q->rc = GT_EBUSY;
+            s->failed++;
+          }
+        s->cv_done.notify_all();
+      }
+      continue;
+    }
+    GraphEntry& ge = s->graphs[gi];
+    const double age = now_us() - ge.pending.front()->t_submit;
+    const size_t want = std::min<size_t>(ge.pending.size(), (size_t)s->cfg.max_batch_roots);
+    if (busy > 0 && want < 64 && age < s->cfg.window_us) {
+      s->cv_sched.wait_for(lk, std::chrono::microseconds((int64_t)std::max(1.0, s->cfg.window_us - age)));
+      continue;
+    }
+    const int words_needed = (int)((want + 63) / 64);
+    while ((int)ge.free_slots.size() < words_needed && grow_slots(s, ge)) {
+    }
+    const int words = std::min<int>(words_needed, (int)ge.free_slots.size());
+    if (words == 0) {  // every lane word of this graph is in flight
+      s->cv_sched.wait_for(lk, std::chrono::microseconds(200));
+      continue;
+    }
+    Flight* f = new Flight();
+    f->srv = s;
+    f->stream = free_stream;
+    f->gid = gi;
+    const size_t take = std::min<size_t>(want, (size_t)words * 64);
+    for (size_t i = 0; i < take; ++i) {
+      f->queries.push_back(ge.pending.front());
+      ge.pending.pop_front();
+    }
+    for (int w = 0; w < words; ++w) {
+      f->slots.push_back(ge.free_slots.back());
+      ge.free_slots.pop_back();
+    }
+    s->flights[free_stream] = f;
+    s->batches++;
+    // build the launch outside the lock
+    std::vector<int64_t> roots(take);
+    std::vector<int32_t*> op(take), ol(take);
+    for (size_t i = 0; i < take; ++i) {
+      roots[i] = f->queries[i]->root;
+      op[i] = f->queries[i]->parent;
+      ol[i] = f->queries[i]->level;
+    }
+    std::vector<SlotSpec> specs(words);
+    for (int w = 0; w < words; ++w) {
+      SlotSpec& sp = specs[w];
+      sp.g = ge.g;
+      sp.mem = ge.slots[f->slots[w]].p;
+      sp.nlanes = (int)std::min<size_t>(64, take - 64 * (size_t)w);
+      sp.roots = roots.data() + 64 * w;
+      sp.outp = op.data() + 64 * w;
+      sp.outl = ol.data() + 64 * w;
+    }
+    cudaStream_t st = s->streams[free_stream];
+    BatchCtx* ctx = &s->ctxs[free_stream];
+    const int share = std::max(1, s->sms / (int)s->streams.size());
+    lk.unlock();
+    int rc = batch_launch(ctx, specs.data(), words, share, st);
+    if (rc == GT_OK) rc = cuda_fail(cudaLaunchHostFunc(st, on_flight_done, f), "host callback");
+    lk.lock();
+    if (rc != GT_OK) {  // nothing will call back: fail the queries here
+      for (int k : f->slots) ge.free_slots.push_back(k);
+      for (Query* q : f->queries) {
+        q->done = true;
+        q->rc = rc;
+        s->failed++;
+      }
+      s->flights[free_stream] = nullptr;
+      delete f;
+      s->cv_done.notify_all();
+    }
+  }
+}
+
+}  // namespace
+}  // namespace gt
+
+using namespace gt;
+
+extern "C" {
+
+GT_API void gt_serve_config_default(gt_serve_config* c) {
+  if (!c) return;
+  memset(c, 0, sizeof(*c));
+  c->hbm_budget_bytes = (int64_t)48 << 30;
+  c->streams = 2;
+  c->max_batch_roots = 256;
+  c->window_us = 200.0;
+}
+
+GT_API int gt_serve_create(const gt_serve_config* cfg, gt_server_t* out) {
+  if (!out) return GT_EINVAL;
+  *out = nullptr;
+  gt_server* s = new (std::nothrow) gt_server();
+  if (!s) return GT_ENOMEM;
+  if (cfg)
+    s->cfg = *cfg;
+  else
+    gt_serve_config_default(&s->cfg);
+  if (s->cfg.streams < 1 || s->cfg.streams > 16 || s->cfg.max_batch_roots < 1 || s->cfg.max_batch_roots > 16384 ||
+      s->cfg.hbm_budget_bytes < 0 || s->cfg.window_us < 0) {
+    delete s;
+    set_error("gt_serve_create: configuration out of range");
+    return GT_EINVAL;
+  }
+  cudaGetDevice(&s->device);
+  cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
+  s->streams.resize(s->cfg.streams);
+  s->ctxs.resize(s->cfg.streams);
+  s->flights.assign(s->cfg.streams, nullptr);
+  for (auto& st : s->streams) {
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      for (auto& t : s->streams)
+        if (t) cudaStreamDestroy(t);
+      delete s;
+      set_error("gt_serve_create: stream creation failed");
+      return GT_EDEVICE;
+    }
+  }
+  s->worker = std::thread(scheduler, s);
+  *out = s;
+  return GT_OK;
+}
+
+GT_API int gt_serve_add_graph(gt_server_t s, gt_graph_t g, int32_t* gid) {
+  if (!s || !g || !gid) return GT_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (g->device != s->device) {
+    set_error("gt_serve_add_graph: graph lives on another device");
+    return GT_EINVAL;
+  }
+  const int64_t need = g->device_bytes + (int64_t)slot_bytes(g);
+  if (s->used_bytes + need > s->cfg.hbm_budget_bytes) {
+    set_error("gt_serve_add_graph: graph plus one lane word of batch storage exceeds the HBM budget");
+    return GT_ENOMEM;
+  }
+  GraphEntry ge;
+  ge.g = g;
+  s->graphs.push_back(ge);
+  s->used_bytes += g->device_bytes;
+  if (!grow_slots(s, s->graphs.back())) {
+    s->used_bytes -= g->device_bytes;
+    s->graphs.pop_back();
+    set_error("gt_serve_add_graph: could not allocate batch storage");
+    return GT_ENOMEM;
+  }
+  *gid = (int32_t)s->graphs.size() - 1;
+  return GT_OK;
+}
+
+GT_API int gt_serve_submit(gt_server_t s, int32_t gid, int64_t root, int32_t* parent, int32_t* level,
+                           uint64_t* ticket) {
+  if (!s || !ticket || !parent || !level) return GT_EINVAL;
+  cudaPointerAttributes pa{}, la{};
+  if (cudaPointerGetAttributes(&pa, parent) != cudaSuccess || cudaPointerGetAttributes(&la, level) != cudaSuccess ||
+      pa.type != cudaMemoryTypeDevice || la.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    set_error("gt_serve_submit: parent and level must be device memory");
+    return GT_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->stop) return GT_EBUSY;
+  if (gid < 0 || gid >= (int32_t)s->graphs.size() || root < 0 || root >= s->graphs[gid].g->n) {
+    set_error("gt_serve_submit: unknown graph id or root outside [0, n)");
+    return GT_EINVAL;
+  }
+  Query* q = new (std::nothrow) Query();
+  if (!q) return GT_ENOMEM;
+  q->ticket = s->next_ticket++;
+  q->gid = gid;
+  q->root = root;
+  q->parent = parent;
+  q->level = level;
+  q->t_submit = now_us();
+  if (s->submitted == 0) s->t_first = q->t_submit;
+  s->submitted++;
+  s->graphs[gid].pending.push_back(q);
+  s->tickets[q->ticket] = q;
+  *ticket = q->ticket;
+  s->cv_sched.notify_all();
+  return GT_OK;
+}
+
+GT_API int gt_serve_poll(gt_server_t s, uint64_t ticket, int32_t timeout_ms) {
+  if (!s) return GT_EINVAL;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->tickets.find(ticket);
+  if (it == s->tickets.end()) {
+    set_error("gt_serve_poll: unknown ticket (never issued or already collected)");
+    return GT_EINVAL;
+  }
+  Query* q = it->second;
+  const auto deadline = Clock::now() + std::chrono::milliseconds(std::max(0, timeout_ms));
+  while (!q->done) {
+    if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && !q->done) return GT_ETIMEOUT;
+  }
+  const int rc = q->rc;
+  s->tickets.erase(it);
+  delete q;
+  return rc;
+}
+
+GT_API int gt_serve_get_stats(gt_server_t s, gt_serve_stats* out) {
+  if (!s || !out) return GT_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  memset(out, 0, sizeof(*out));
+  out->submitted = s->submitted;
+  out->completed = s->completed;
+  out->failed = s->failed;
+  out->batches = s->batches;
+  for (auto* f : s->flights) out->inflight += f ? 1 : 0;
+  for (auto& ge : s->graphs) out->pending += (int64_t)ge.pending.size();
+  out->device_bytes = s->used_bytes;
+  if (!s->lat_us.empty()) {
+    std::vector<double> v = s->lat_us;
+    std::sort(v.begin(), v.end());
+    auto pct = [&](double p) { return v[std::min(v.size() - 1, (size_t)(p * (v.size() - 1) + 0.5))]; };
+    out->p50_us = pct(0.50);
+    out->p99_us = pct(0.99);
+    out->max_us = v.back();
+    double sum = 0;
+    for (double x : v) sum += x;
+    out->mean_us = sum / v.size();
+    const double span = s->t_last - s->t_first;
+    out->qps = span > 0 ? s->completed / (span * 1e-6) : 0;
+  }
+  return GT_OK;
+}
+
+GT_API int gt_serve_reset_stats(gt_server_t s) {
+  if (!s) return GT_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->lat_us.clear();
+  s->submitted = s->completed = s->failed = s->batches = 0;
+  s->t_first = s->t_last = 0;
+  return GT_OK;
+}
+
+GT_API int gt_serve_destroy(gt_server_t s) {
+  if (!s) return GT_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv_sched.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  for (auto st : s->streams) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
+  for (auto& c : s->ctxs) batch_ctx_free(&c);
+  for (auto& ge : s->graphs)
+    for (auto& b : ge.slots)
+      for (int i = 0; i < 7; ++i) cudaFree(b.p[i]);
+  for (auto& kv : s->tickets) delete kv.second;
+  delete s;
+  return GT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,123 @@
+"""Serving with continuous batching through the C-ABI: queries arriving from several
+threads at random times over several resident graphs; every result must equal the
+single-root answer (alone) bit for bit, and the server's host-side failure paths answer
+with status codes (no GPU fault is ever provoked)."""
+import random
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import graphgen
+import paper_2009_07463_gb300 as gt
+from oracle import OracleGraph
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available()
+    return t
+
+
+@pytest.fixture(scope="module")
+def graphs():
+    out = []
+    for i, (kind, a) in enumerate([("rmat", 12), ("rmat", 14), ("uniform", 30000), ("rmat", 10)]):
+        if kind == "rmat":
+            n = 1 << a
+            e = graphgen.rmat_edges(a, 16, seed=70 + i)
+        else:
+            n = a
+            e = graphgen.uniform_edges(n, n * 8, seed=70 + i)
+        g = gt.gt_graph_build(e, n, mh=[0, 1, 0, -1][i])
+        out.append((g, OracleGraph(e, n)))
+    return out
+
+
+def test_results_same_alone_and_in_the_mix(torch, graphs):
+    srv = gt.Server(streams=2, max_batch_roots=128, window_us=300)
+    gids = [srv.add_graph(g) for g, _ in graphs]
+    rng = random.Random(5)
+    jobs = []
+    for k in range(240):
+        gi = rng.randrange(len(graphs))
+        g, og = graphs[gi]
+        deg = og.degree()
+        root = rng.randrange(g.n)
+        jobs.append((gi, root))
+    bufs = [(torch.full((graphs[gi][0].n,), -7, dtype=torch.int32, device="cuda"),
+             torch.full((graphs[gi][0].n,), -7, dtype=torch.int32, device="cuda")) for gi, _ in jobs]
+    torch.cuda.synchronize()
+    tickets = [None] * len(jobs)
+
+    def producer(idx):
+        for j in idx:
+            gi, root = jobs[j]
+            tickets[j] = srv.submit(gids[gi], root, bufs[j][0], bufs[j][1])
+            time.sleep(rng.random() * 0.0005)
+
+    threads = [threading.Thread(target=producer, args=(list(range(t, len(jobs), 4)),)) for t in range(4)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    for j, t in enumerate(tickets):
+        assert srv.poll(t, 30000) == gt.GT_OK
+    st = srv.stats()
+    assert st["completed"] == len(jobs) and st["failed"] == 0 and st["batches"] >= 2
+    assert st["p99_us"] >= st["p50_us"] > 0
+    for j, (gi, root) in enumerate(jobs):
+        g, og = graphs[gi]
+        p_alone, l_alone = g.bfs(root)
+        assert np.array_equal(bufs[j][1].cpu().numpy(), l_alone), f"query {j} level differs from gt_bfs alone"
+        assert np.array_equal(bufs[j][0].cpu().numpy(), p_alone), f"query {j} parent differs from gt_bfs alone"
+        if j % 20 == 0:
+            wl, wp = og.bfs(root)
+            assert np.array_equal(l_alone, wl) and np.array_equal(p_alone, wp)
+    srv.destroy()
+
+
+def test_budget_admission_and_errors(torch, graphs):
+    g, _ = graphs[1]
+    small = gt.Server(hbm_budget_bytes=1 << 20)
+    with pytest.raises(gt.GtError) as ei:
+        small.add_graph(g)
+    assert ei.value.code == gt.GT_ENOMEM
+    small.destroy()
+    srv = gt.Server()
+    gid = srv.add_graph(g)
+    p = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    l = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    with pytest.raises(gt.GtError) as ei:
+        srv.submit(gid, g.n, p, l)  # root out of range
+    assert ei.value.code == gt.GT_EINVAL
+    with pytest.raises(gt.GtError):
+        srv.submit(gid + 5, 0, p, l)  # unknown graph
+    hp = np.empty(g.n, dtype=np.int32)
+    with pytest.raises(gt.GtError):
+        srv.submit(gid, 0, hp, hp)  # host buffers are refused
+    with pytest.raises(gt.GtError):
+        srv.poll(123456789, 0)  # unknown ticket
+    t = srv.submit(gid, 3, p, l)
+    rc = srv.poll(t, 0)
+    assert rc in (gt.GT_OK, gt.GT_ETIMEOUT)
+    if rc == gt.GT_ETIMEOUT:
+        assert srv.poll(t, 30000) == gt.GT_OK
+    pa, la = g.bfs(3)
+    assert np.array_equal(l.cpu().numpy(), la) and np.array_equal(p.cpu().numpy(), pa)
+    srv.destroy()
+
+
+def test_destroy_with_queries_outstanding(torch, graphs):
+    g, _ = graphs[0]
+    srv = gt.Server(streams=1)
+    gid = srv.add_graph(g)
+    bufs = [(torch.empty(g.n, dtype=torch.int32, device="cuda"), torch.empty(g.n, dtype=torch.int32, device="cuda"))
+            for _ in range(50)]
+    for k in range(50):
+        srv.submit(gid, k, *bufs[k])
+    srv.destroy()  # finishes what is in flight, fails the rest, returns
