@@ -219,6 +219,24 @@ GT_API int gt_serve_reset_stats(gt_server_t s);
  * frees the server (not the graphs). */
 GT_API int gt_serve_destroy(gt_server_t s);
 
+/* ---- Traversal that allocates nothing (the paper has no counterpart) ----
+ * For callers that cannot allocate device memory when they need a traversal: a service
+ * whose memory plan is fixed at start-up and forbids allocation on the request path (an
+ * allocation can block, synchronise the device or fail once memory is fragmented), or a
+ * plug-in inside a framework that owns all device memory and passes only inputs and
+ * outputs. Runs the plain direction-optimizing BFS (same results as gt_bfs_plain) on the
+ * caller's device CSR: row int64[n+1], col int32[row[n]] (sorted, symmetric, no
+ * self-loops), writing the device int32[n] parent and level arrays. All scratch lives in
+ * one file-scope device array of about 12 MB, reserved on every device that loads the
+ * library until the process exits, so n is limited to 262,144 vertices (GT_EINVAL above).
+ * No cudaMalloc, cudaFree or allocating library routine is called. The first call on a
+ * device looks up the array's device address; make that first call before any stream
+ * capture. Every call uses the same array, so calls that overlap on the GPU (other
+ * streams, other threads) race and must be serialised by the caller. Synchronises
+ * `stream` once per level. */
+GT_API int gt_bfs_csr_noalloc(const int64_t* row, const int32_t* col, int64_t n, int64_t root, int32_t* parent,
+                              int32_t* level, void* stream);
+
 GT_API const char* gt_strerror(int code);
 GT_API const char* gt_last_error(void);
 

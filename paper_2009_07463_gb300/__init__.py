@@ -84,6 +84,7 @@ def lib():
                 "gt_bfs_plain": (ctypes.c_int, [p, i64, p, p, p]),
                 "gt_bfs_trace": (ctypes.c_int, [p, p, i32, p]),
                 "gt_bfs_timing": (ctypes.c_int, [p, p]),
+                "gt_bfs_csr_noalloc": (ctypes.c_int, [p, p, i64, i64, p, p, p]),
                 "gt_bfs_batch": (ctypes.c_int, [p, i32, p, p, p, p, p]),
                 "gt_autotune": (ctypes.c_int, [p, i32, ctypes.c_uint64, p, p]),
                 "gt_serve_config_default": (None, [p]),
@@ -359,6 +360,13 @@ class Server:
             self.destroy()
         except Exception:
             pass
+
+
+def gt_bfs_csr_noalloc(row, col, n: int, root: int, parent, level, stream=None) -> None:
+    """Plain BFS on a caller's device CSR without any device allocation (fixed scratch;
+    n <= 262,144); same results as gt_bfs_plain."""
+    _check(lib().gt_bfs_csr_noalloc(_ptr(row), _ptr(col), int(n), int(root), _ptr(parent), _ptr(level),
+                                    _stream(stream)), "gt_bfs_csr_noalloc")
 
 
 def gt_count_traversed(edges, level, stream=None, m: int | None = None) -> int:

@@ -12,6 +12,8 @@
 // unvisited vertex), which is the smallest one. Both directions therefore give the
 // same levels and min-id parents, whatever the switch does.
 #include <algorithm>
+#include <mutex>
+#include <string>
 
 #include "gt_device.cuh"
 #include "gt_internal.cuh"
@@ -986,4 +988,136 @@ int run_bfs(gt_graph* g, View& v, bool et, int64_t root, int32_t* parent, int32_
   return rc;
 }
 
+// ---- Traversal that allocates nothing ------------------------------------------------------
+// Some callers cannot allocate device memory when they need a traversal: a service that
+// fixes its memory plan at start-up and forbids allocation on the request path (an
+// allocation can block, synchronise the device, or fail once memory is fragmented), or a
+// plug-in running inside a host framework that owns all device memory and hands the
+// plug-in only its inputs and outputs. gt_bfs_csr_noalloc serves them: the plain
+// direction-optimizing traversal of a caller's device CSR, with every piece of scratch
+// (per-vertex state, visited bitmaps, frontier queues, control block) carved from the one
+// file-scope array below. That array is reserved on each device when the library's code
+// is loaded there and stays reserved until the process exits.
+constexpr int64_t NOALLOC_MAX_N = int64_t(1) << 18;       // largest graph: 262,144 vertices
+constexpr int64_t NOALLOC_WORDS = NOALLOC_MAX_N / 32;     // a multiple of BU_CHUNK_WORDS
+constexpr size_t NOALLOC_CTL_BYTES = (sizeof(BfsCtl) + 255) & ~size_t(255);
+constexpr size_t NOALLOC_BYTES = NOALLOC_CTL_BYTES + 8 * NOALLOC_MAX_N          // state
+                                 + 2 * 4 * NOALLOC_WORDS                        // two bitmaps
+                                 + 4 * NOALLOC_MAX_N * 2 * NBINS                // queue sets
+                                 + 4 * NOALLOC_MAX_N;                           // unvisited list
+static_assert(NOALLOC_WORDS % BU_CHUNK_WORDS == 0, "bitmap words must fill whole chunks");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+namespace {
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the scratch array on the current device. Host code cannot use the
+// array's name as an address (it names a host-side shadow), so the address is looked up
+// once per device with that device current and cached.
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  int rc = cuda_fail(cudaGetDevice(&dev), "cudaGetDevice");
+  if (rc) return rc;
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+    set_error("gt_bfs_csr_noalloc: device index beyond the supported range");
+    return GT_ENOTSUP;
+  }
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    rc = cuda_fail(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress of the traversal scratch");
+    if (rc) return rc;
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return GT_OK;
+}
+
+bool on_device(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
 }  // namespace gt
+
+extern "C" GT_API int gt_bfs_csr_noalloc(const int64_t* row, const int32_t* col, int64_t n, int64_t root,
+                                         int32_t* parent, int32_t* level, void* stream) {
+  using namespace gt;
+  if (!row || !col || !parent || !level || n < 1 || root < 0 || root >= n) {
+    set_error("gt_bfs_csr_noalloc: null pointer, n < 1 or root outside [0, n)");
+    return GT_EINVAL;
+  }
+  if (n > NOALLOC_MAX_N) {
+    set_error("gt_bfs_csr_noalloc: n = " + std::to_string(n) + " exceeds the fixed scratch capacity of " +
+              std::to_string(NOALLOC_MAX_N) + " vertices");
+    return GT_EINVAL;
+  }
+  if (!on_device(row) || !on_device(col) || !on_device(parent) || !on_device(level)) {
+    set_error("gt_bfs_csr_noalloc: row, col, parent and level must be device memory");
+    return GT_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  void* base = nullptr;
+  int rc = noalloc_scratch(&base);
+  if (rc) return rc;
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t nnz = 0;
+  rc = cuda_fail(cudaMemcpyAsync(&nnz, row + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s), "read nnz");
+  if (!rc) rc = cuda_fail(cudaStreamSynchronize(s), "sync");
+  if (rc) return rc;
+  // carve the views of one traversal out of the array
+  unsigned char* p = (unsigned char*)base;
+  View v;
+  v.n = n;
+  v.nnz = nnz;
+  v.nwords = ((n + 31) / 32 + BU_CHUNK_WORDS - 1) / BU_CHUNK_WORDS * BU_CHUNK_WORDS;
+  v.row = const_cast<int64_t*>(row);
+  v.col = const_cast<int32_t*>(col);
+  v.ctl = (BfsCtl*)p;
+  p += NOALLOC_CTL_BYTES;
+  v.state = (uint64_t*)p;
+  p += 8 * NOALLOC_MAX_N;
+  v.vis[0] = (uint32_t*)p;
+  p += 4 * NOALLOC_WORDS;
+  v.vis[1] = (uint32_t*)p;
+  p += 4 * NOALLOC_WORDS;
+  v.queues = (int32_t*)p;
+  p += 4 * NOALLOC_MAX_N * 2 * NBINS;
+  v.ulist = (int32_t*)p;
+  gt_tuning t;
+  gt_tuning_default(&t);
+  const BfsArgs a = make_args(v, t);
+  const int grid = sms * std::max(1, t.blocks_per_sm);
+  // state and the first bitmap start cleared; the control block is rewritten by the start
+  // kernel; queue and list entries are only read below the counts the kernels set
+  bfs_reset<<<std::max(1, (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8)), 256, 0, s>>>(
+      v.state, v.vis[0], v.n, v.nwords);
+  bfs_start_plain<<<1, 1, 0, s>>>(a, (int32_t)root, t.alpha, t.beta, 0);
+  struct Head {
+    int32_t level, dir, done, cur, vcur, need_mark, need_queue;
+  } h{};
+  for (int64_t guard = 0; guard <= n + 1; ++guard) {  // at most one step per level
+    rc = cuda_fail(cudaMemcpyAsync(&h, v.ctl, sizeof(h), cudaMemcpyDeviceToHost, s), "ctl readback");
+    if (!rc) rc = cuda_fail(cudaStreamSynchronize(s), "level sync");
+    if (rc) return rc;
+    if (h.done) break;
+    launch_step(h.dir == DIR_TD ? (h.need_queue ? 3 : 0) : (h.need_mark ? 2 : 1), a, grid, s);
+    bfs_decide<<<1, 1, 0, s>>>(a, 0, 0);
+    rc = cuda_fail(cudaGetLastError(), "level launch");
+    if (rc) return rc;
+  }
+  plain_output<<<std::max(1, (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8)), 256, 0, s>>>(
+      v.state, v.n, parent, level);
+  return cuda_fail(cudaGetLastError(), "noalloc output");
+}
