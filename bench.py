@@ -56,6 +56,11 @@ def parse():
     ap.add_argument("--trace-out", default="")
     ap.add_argument("--launch-mode", default="graph", choices=["graph", "host"],
                     help="host: one launch per kernel (lets ncu see every kernel; slower)")
+    ap.add_argument("--workload", default="et", choices=["et", "batch", "serve"],
+                    help="et: single-root edge-tree BFS (the headline line); batch: 64-root lane words "
+                         "on scale 24 plus a mixed 32-graph batch; serve: Poisson queries on 12 resident graphs")
+    ap.add_argument("--serve-rates", default="4000,16000,48000")
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
     return ap.parse_args()
 
 
@@ -75,8 +80,10 @@ def hmean(x):
 
 # ---- CPU oracle leg (spawned process; never touches the GPU) -----------------------------
 
-def oracle_job(scale, edgefactor, seed, root_seed, nroots, warm, q):
-    """Builds the oracle graph (untimed), then times serial oracle BFS from nroots roots."""
+def oracle_job(scale, edgefactor, seed, root_seed, nroots, warm, q, go):
+    """Builds the oracle graph (untimed), then times serial oracle BFS from nroots roots.
+    Waits for `go`, so its host memory traffic never overlaps the GPU's timed passes."""
+    go.wait()
     try:
         import graphgen
         from oracle import OracleGraph, traversed_tuples
@@ -102,13 +109,15 @@ def oracle_job(scale, edgefactor, seed, root_seed, nroots, warm, q):
 def start_oracle(a, nroots, warm):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
-    p = ctx.Process(target=oracle_job, args=(a.scale, a.edgefactor, a.seed, a.root_seed, nroots, warm, q),
+    go = ctx.Event()
+    p = ctx.Process(target=oracle_job, args=(a.scale, a.edgefactor, a.seed, a.root_seed, nroots, warm, q, go),
                     daemon=True)
     p.start()
-    return p, q
+    return p, q, go
 
 
-def oracle_result(p, q, timeout):
+def oracle_result(p, q, go, timeout):
+    go.set()
     try:
         r = q.get(timeout=timeout)
     except Exception:
@@ -231,6 +240,27 @@ def launches_of(trace: list[dict]) -> int:
     return k
 
 
+# ---- replicas (N > 1): each rank holds a full graph and takes its own roots -------------
+
+def rank_roots(all_roots, rank: int, per_rank: int) -> list[int]:
+    """Rank r's share of the seeded roots: entries [r * per_rank, (r + 1) * per_rank)."""
+    return [int(x) for x in all_roots[rank * per_rank:(rank + 1) * per_rank]]
+
+
+def combine_ranks(ms_per_step: float, hm: float, dist, device):
+    """Whole-job numbers: the slowest rank's time per step, and N x the harmonic mean of
+    the ranks' GTEPS (N replicas run concurrently, each at its own rate). No data-path
+    collective: this is the only exchange, after the timed region."""
+    if dist is None:
+        return ms_per_step, hm
+    import torch
+    world = dist.get_world_size()
+    t = torch.tensor([ms_per_step, hm], dtype=torch.float64, device=device)
+    gathered = [torch.zeros_like(t) for _ in range(world)]
+    dist.all_gather(gathered, t)
+    return max(float(x[0]) for x in gathered), world * hmean([float(x[1]) for x in gathered])
+
+
 # ---- main ---------------------------------------------------------------------------------
 
 def main():
@@ -240,6 +270,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if a.impl == "reference":
         return run_reference(a, world, rank)
+    if a.workload == "batch":
+        return run_batch_workload(a, rank, local)
+    if a.workload == "serve":
+        return run_serve_workload(a, rank, local)
 
     # the oracle leg is spawned before the first GPU call
     oracle = None
@@ -276,7 +310,7 @@ def main():
     st = g.stats()
     deg = g.degree()
     all_roots = graphgen.pick_roots(a.root_seed, n, a.roots * world, deg)
-    roots = all_roots[rank * a.roots:(rank + 1) * a.roots].tolist()
+    roots = rank_roots(all_roots, rank, a.roots)
 
     parent = torch.empty(n, dtype=torch.int32, device=dev)
     level = torch.empty(n, dtype=torch.int32, device=dev)
@@ -326,15 +360,7 @@ def main():
     hm = hmean(gteps)
     am = sum(gteps) / len(gteps)
     ms_per_step = total_ms / a.steps
-    if dist:
-        t = torch.tensor([ms_per_step, hm], dtype=torch.float64, device=dev)
-        gathered = [torch.zeros_like(t) for _ in range(world)]
-        dist.all_gather(gathered, t)
-        ms_per_step = max(float(x[0]) for x in gathered)
-        hm_all = hmean([float(x[1]) for x in gathered])
-        value = world * hm_all
-    else:
-        value = hm
+    ms_per_step, value = combine_ranks(ms_per_step, hm, dist, dev)
     launches_per_step = sum(launches_of(tr) for tr in traces)
 
     out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -371,6 +397,8 @@ def main():
                       "how": "gt_bfs with pinned host parent/level buffers; D2H copy and stream sync inside each "
                              "timed call; root passed by value"}
 
+        if oracle is not None:
+            oracle[2].set()  # the timed and e2e passes are done: the CPU leg may start
         # roofline of the bottom-up kernel: work counts, then CUDA-event durations per launch
         g.set_tuning(count_work=1, launch_mode=1)
         counted = []
@@ -470,6 +498,209 @@ def run_reference(a, world, rank):
                             "sample": f"one seeded root per step on the same scale-{a.scale} graph; serial oracle "
                                       f"BFS; oracle graph built untimed in {setup:.0f} s"},
            "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---- batched and served workloads -------------------------------------------------------
+
+def _make_graph(gt, graphgen, torch, kind, a_, seed, dev):
+    """R-MAT (kind 'rmat', a_ = scale, edge factor 16) or uniform (a_ = (n, avg degree))."""
+    if kind == "rmat":
+        n, m = 1 << a_, 16 << a_
+        e = torch.empty((m, 2), dtype=torch.int64, device=dev)
+        graphgen.rmat_edges_device(e.data_ptr(), a_, m, seed=seed)
+    else:
+        n, d = a_
+        m = n * d // 2
+        e = torch.empty((m, 2), dtype=torch.int64, device=dev)
+        graphgen.uniform_edges_device(e.data_ptr(), n, m, seed=seed)
+    torch.cuda.synchronize()
+    g = gt.gt_graph_build(e, n)
+    return g, e
+
+
+def run_batch_workload(a, rank, local):
+    """Config 4: 64 roots in one lane word on R-MAT scale 24, and a mixed batch of 32 graphs
+    (R-MAT scales 14-22, uniform graphs of average degree 16), 64 roots each, every batch in
+    one persistent launch with autotuned parameters; against the same roots run one at a
+    time with gt_bfs. Queries/s and GTEPS-equivalent (traversed tuples / time)."""
+    import torch
+
+    import graphgen
+    import paper_2009_07463_gb300 as gt
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    res = {}
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def measure(specs, label):
+        graphs, roots, tuples = [], [], []
+        for i, (kind, arg) in enumerate(specs):
+            g, e = _make_graph(gt, graphgen, torch, kind, arg, 100 + i, dev)
+            g.autotune(nsample=4, seed=7)
+            r = graphgen.pick_roots(3 + i, g.n, 64, g.degree()).tolist()
+            lv = torch.empty(g.n, dtype=torch.int32, device=dev)
+            pa = torch.empty(g.n, dtype=torch.int32, device=dev)
+            tt = []
+            for x in r:
+                g.bfs(x, pa, lv)
+                tt.append(gt.gt_count_traversed(e, lv))
+            del e
+            graphs.append(g)
+            roots.append(r)
+            tuples.append(tt)
+        outs_p = [torch.empty((64, g.n), dtype=torch.int32, device=dev) for g in graphs]
+        outs_l = [torch.empty((64, g.n), dtype=torch.int32, device=dev) for g in graphs]
+        ms_batch = timed(lambda: gt.gt_bfs_batch(graphs, roots, outs_p, outs_l), 3)
+        lv = torch.empty(max(g.n for g in graphs), dtype=torch.int32, device=dev)
+        pa = torch.empty_like(lv)
+
+        def seq():
+            for g, r in zip(graphs, roots):
+                for x in r:
+                    g.bfs(x, pa[:g.n], lv[:g.n])
+        ms_seq = timed(seq, 1)
+        nq = sum(len(r) for r in roots)
+        te = sum(sum(t) for t in tuples)
+        res[label] = {"queries": nq, "batch_ms": round(ms_batch, 3), "sequential_ms": round(ms_seq, 3),
+                      "batch_qps": round(nq / ms_batch * 1e3, 1), "sequential_qps": round(nq / ms_seq * 1e3, 1),
+                      "batch_gteps_equiv": round(te / ms_batch / 1e6, 1),
+                      "sequential_gteps_equiv": round(te / ms_seq / 1e6, 1),
+                      "speedup": round(ms_seq / ms_batch, 2)}
+        del outs_p, outs_l
+        for g in graphs:
+            g.free()
+        torch.cuda.empty_cache()
+
+    measure([("rmat", 24)], "rmat_s24_64_roots")
+    mixed = [("rmat", 14 + (i % 9)) for i in range(24)] + [("uniform", (1 << (15 + (i % 6)), 16)) for i in range(8)]
+    measure(mixed, "mixed_32_graphs_64_roots_each")
+    out = {"metric": "batched BFS queries/s (64-root lane words, one persistent launch)",
+           "value": res["mixed_32_graphs_64_roots_each"]["batch_qps"], "unit": "queries/s", "n_gpus": 1,
+           "higher_is_better": True, "dtype": "int32", "data": "synthetic",
+           "config": {"workload": "batch: rmat s24 x 64 roots; 32 mixed graphs (rmat s14-22, uniform deg 16) x 64 roots",
+                      "autotuned": True}, "results": res}
+    print(json.dumps(out), flush=True)
+
+
+def run_serve_workload(a, rank, local):
+    """Config 5: 12 resident graphs (R-MAT scales 18-25 at edge factor 16; uniform graphs of
+    average degree 8-32), a 48 GiB HBM budget, Poisson arrivals of single-root queries at
+    each stated rate (roots uniform over vertices of degree >= 1 of a uniformly chosen
+    graph). Served with continuous batching vs the same arrival schedule run by one worker
+    with sequential gt_bfs calls. Queries/s and p50/p99 latency (arrival -> results ready)."""
+    import threading
+    import numpy as np
+    import torch
+
+    import graphgen
+    import paper_2009_07463_gb300 as gt
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    specs = [("rmat", s) for s in range(18, 26)] + [("uniform", (1 << 20, d)) for d in (8, 16, 24, 32)]
+    graphs, cand = [], []
+    for i, (kind, arg) in enumerate(specs):
+        g, e = _make_graph(gt, graphgen, torch, kind, arg, 200 + i, dev)
+        del e
+        graphs.append(g)
+        cand.append(np.flatnonzero(g.degree() > 0))
+    torch.cuda.empty_cache()
+    RING = 64
+    bufs = [[(torch.empty(g.n, dtype=torch.int32, device=dev), torch.empty(g.n, dtype=torch.int32, device=dev))
+             for _ in range(RING)] for g in graphs]
+    rng = np.random.default_rng(11)
+    rates = [float(x) for x in a.serve_rates.split(",") if x]
+    results = []
+    for rate in rates:
+        nq = int(rate * a.serve_seconds)
+        gaps = rng.exponential(1.0 / rate, size=nq)
+        gsel = rng.integers(0, len(graphs), size=nq)
+        roots = [int(cand[gi][rng.integers(0, cand[gi].size)]) for gi in gsel]
+        # served
+        srv = gt.Server(hbm_budget_bytes=48 << 30, streams=2, max_batch_roots=128, window_us=100)
+        gids = [srv.add_graph(g) for g in graphs]
+        slot_busy = [[None] * RING for _ in graphs]
+        ring_pos = [0] * len(graphs)
+        lat = [0.0] * nq
+        t_arr = [0.0] * nq
+        tickets = [None] * nq
+        done_ev = threading.Event()
+
+        def collector():
+            for j in range(nq):
+                while tickets[j] is None:
+                    time.sleep(0.00005)
+                srv.poll(tickets[j], 60000)
+                lat[j] = time.perf_counter() - t_arr[j]
+            done_ev.set()
+        col = threading.Thread(target=collector)
+        col.start()
+        t0 = time.perf_counter()
+        t_next = t0
+        for j in range(nq):
+            t_next += gaps[j]
+            while time.perf_counter() < t_next:
+                pass
+            gi = int(gsel[j])
+            k = ring_pos[gi]
+            ring_pos[gi] = (k + 1) % RING
+            prev = slot_busy[gi][k]
+            if prev is not None:
+                while lat[prev] == 0.0:  # ring buffer still owned by an earlier query
+                    time.sleep(0.00002)
+            slot_busy[gi][k] = j
+            t_arr[j] = t_next
+            p, l = bufs[gi][k]
+            tickets[j] = srv.submit(gids[gi], roots[j], p, l)
+        done_ev.wait()
+        st = srv.stats()  # latency stamped by the completion callback: submit -> results ready
+        srv.destroy()
+        col.join()
+        served = {"qps": round(st["qps"], 1), "p50_us": round(st["p50_us"], 1), "p99_us": round(st["p99_us"], 1),
+                  "batches": st["batches"], "mean_batch": round(nq / max(st["batches"], 1), 1)}
+        # sequential single-root calls on the same schedule (one worker, FIFO)
+        lat2 = []
+        stream = torch.cuda.current_stream()
+        t0 = time.perf_counter()
+        t_arr2 = t0
+        for j in range(nq):
+            t_arr2 += gaps[j]
+            now = time.perf_counter()
+            if now < t_arr2:
+                while time.perf_counter() < t_arr2:
+                    pass
+            gi = int(gsel[j])
+            p, l = bufs[gi][j % RING]
+            graphs[gi].bfs(roots[j], p, l, stream=stream)
+            stream.synchronize()
+            lat2.append(time.perf_counter() - t_arr2)
+        t_end2 = t_arr2 + lat2[-1]
+        lat2s = sorted(lat2)
+        seq = {"qps": round(nq / (t_end2 - t0), 1), "p50_us": round(1e6 * lat2s[nq // 2], 1),
+               "p99_us": round(1e6 * lat2s[min(nq - 1, int(0.99 * nq))], 1)}
+        results.append({"rate_qps": rate, "queries": nq, "served": served, "sequential": seq})
+    best = max(results, key=lambda r: r["served"]["qps"])
+    out = {"metric": "served BFS queries/s and p99 latency (continuous batching)", "value": best["served"]["qps"],
+           "unit": "queries/s", "p99_us": best["served"]["p99_us"], "n_gpus": 1, "higher_is_better": True,
+           "dtype": "int32", "data": "synthetic",
+           "config": {"workload": "serve: 12 resident graphs (rmat s18-25 ef16, uniform 2^20 deg 8/16/24/32), "
+                                  "Poisson arrivals", "hbm_budget_gib": 48, "streams": 2, "max_batch_roots": 128,
+                      "window_us": 100, "seconds_per_rate": a.serve_seconds},
+           "rates": results}
     print(json.dumps(out), flush=True)
 
 

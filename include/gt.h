@@ -61,7 +61,7 @@ typedef struct gt_config {
 
 /* Run-time tuning of the traversal; results never depend on it. */
 typedef struct gt_tuning {
-  int32_t alpha;        /* top-down -> bottom-up when m_f * alpha > m_u (default 64) */
+  int32_t alpha;        /* top-down -> bottom-up when m_f * alpha > m_u (default 32) */
   int32_t beta;         /* bottom-up -> top-down when n_f * beta < n and shrinking (256) */
   int32_t td_warp_min;  /* top-down: degree above which a whole warp takes a vertex (32) */
   int32_t td_cta_min;   /* top-down: degree above which a whole CTA takes a vertex (256) */
@@ -134,8 +134,10 @@ GT_API int gt_graph_set_tuning(gt_graph_t g, const gt_tuning* t);
 
 /* Edge-tree BFS from `root` (Alg. 9): root-in-tree walk to its core vertex, BFS on the
  * core only, then edge-tree resolution. parent and level are int32[n], both device or
- * both host memory; with host memory the call copies the result back and returns after
- * `stream` has finished. */
+ * both host memory. With page-locked host memory (cudaHostAlloc / registered) the output
+ * pass writes the result straight into it; with pageable host memory the result is
+ * staged on the device and copied back. With host memory the call returns after `stream`
+ * has finished. */
 GT_API int gt_bfs(gt_graph_t g, int64_t root, int32_t* parent, int32_t* level, void* stream);
 /* The same contract on the unsplit graph (plain direction-optimizing BFS, Alg. 1); the
  * comparison baseline. GT_ENOTSUP if the handle was built with keep_plain = 0. */

@@ -35,6 +35,10 @@ namespace {
 constexpr int BT = 256;
 constexpr int BW = BT / 32;
 constexpr int MAX_SLOTS_SMEM = 256;
+// Neighbours a lane scans alone (two dependent loads each) before its warp continues the
+// scan 32 entries per step; multi-source scans rarely stop early, so most of the work is
+// best done by the coalesced warp-wide path.
+constexpr int THREAD_SCAN = 4;
 
 struct LaneInit {
   int32_t start;    // core id the lane's BFS starts from (-1: nothing to traverse)
@@ -266,7 +270,7 @@ __global__ void __launch_bounds__(BT) batch_run(SlotDev* slots, SlotCtl* sctl, i
             if (miss) {
               b = s.crow[w];
               e = s.crow[w + 1];
-              got = first_hits_thread(s, fc, w, miss, b, min(e, b + 32), &stop);
+              got = first_hits_thread(s, fc, w, miss, b, min(e, b + THREAD_SCAN), &stop);
             }
           }
           unsigned lm = __ballot_sync(FULL, miss && got != miss && stop < e);
@@ -315,7 +319,7 @@ __global__ void __launch_bounds__(BT) batch_run(SlotDev* slots, SlotCtl* sctl, i
           b = s.crow[w];
           e = s.crow[w + 1];
           msum += e - b;
-          if (s_dir[si] == DIR_TD) got = first_hits_thread(s, fc, w, nb, b, min(e, b + 32), &stop);
+          if (s_dir[si] == DIR_TD) got = first_hits_thread(s, fc, w, nb, b, min(e, b + THREAD_SCAN), &stop);
           else got = nb;
         }
         unsigned lm = __ballot_sync(FULL, w >= 0 && got != nb);

@@ -1,7 +1,8 @@
 // bfs.cu -- direction-optimizing BFS (Alg. 1) on a CSR view, and the edge-tree steps
 // around it (Alg. 9: root walk to the core, BFS_CORE, edge-tree resolution).
 //
-// Per-vertex state is one 64-bit word (level << 32 | parent), UNVISITED = all ones.
+// Per-vertex state is one 64-bit word (level << 32 | parent's vertex id), UNVISITED = all
+// ones. Views of the core use core ids for traversal and vertex ids for parents.
 // Top-down (Alg. 1 TOP-DOWN): every frontier edge to a vertex that was not visited at
 // the start of the level does atomicMin(state, (L+1) << 32 | v); the smallest packed
 // value wins, i.e. level L+1 with the smallest frontier neighbour as parent, and the
@@ -34,6 +35,7 @@ struct BfsArgs {
   uint32_t* vis1;
   int32_t* queues;  // [2][NBINS][n]
   int32_t* ulist;
+  const int32_t* new2old;  // view id -> vertex id (null: the view's ids are vertex ids)
   BfsCtl* ctl;
   int32_t td_warp_min;
   int32_t td_cta_min;
@@ -54,6 +56,7 @@ BfsArgs make_args(const View& v, const gt_tuning& t) {
   a.vis1 = v.vis[1];
   a.queues = v.queues;
   a.ulist = v.ulist;
+  a.new2old = v.new2old;
   a.ctl = v.ctl;
   a.td_warp_min = std::max(1, t.td_warp_min);
   a.td_cta_min = std::max(a.td_warp_min, t.td_cta_min);
@@ -65,6 +68,12 @@ BfsArgs make_args(const View& v, const gt_tuning& t) {
 
 __device__ __forceinline__ int32_t* queue_of(const BfsArgs& a, int set, int bin) {
   return a.queues + ((int64_t)(set * NBINS + bin)) * (a.n > 0 ? a.n : 1);
+}
+
+// The state keeps parents as vertex ids, so the output pass needs no translation. The
+// core relabel is monotone, so the smallest vertex id is also the smallest view id.
+__device__ __forceinline__ uint32_t orig_of(const BfsArgs& a, int32_t v) {
+  return a.new2old ? (uint32_t)a.new2old[v] : (uint32_t)v;
 }
 
 __device__ __forceinline__ int bin_of(const BfsArgs& a, int64_t d) {
@@ -89,6 +98,46 @@ __device__ __forceinline__ void warp_enqueue(bool disc, int32_t w, int64_t wdeg,
     base = __shfl_sync(FULL, base, leader);
     if (b == k) queue_of(a, set, k)[base + __popc(mk & lanemask_lt())] = w;
   }
+}
+
+// Per-warp staging of discovered vertices in shared memory: a warp collects up to STG
+// vertices per degree bin and appends them to the global queue with one atomic per
+// flush, instead of one same-address atomic per warp step.
+constexpr int STG = 128;
+
+struct StageQ {
+  int32_t* buf;     // this warp's shared buffer, [NBINS][STG]
+  int cnt[NBINS];   // entries held per bin (the same in every lane)
+};
+
+__device__ __forceinline__ void stage_flush(StageQ& sq, int k, const BfsArgs& a, int set, int64_t* bin_n) {
+  const int c = sq.cnt[k];
+  if (c == 0) return;
+  const int lane = threadIdx.x & 31;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd((unsigned long long*)&bin_n[k], (unsigned long long)c);
+  base = __shfl_sync(FULL, base, 0);
+  __syncwarp();
+  int32_t* q = queue_of(a, set, k);
+  for (int i = lane; i < c; i += 32) q[base + i] = sq.buf[k * STG + i];
+  __syncwarp();
+  sq.cnt[k] = 0;
+}
+
+// Stages the lanes with `disc` set, each in its degree bin. All 32 lanes must call.
+__device__ __forceinline__ void stage_push(StageQ& sq, bool disc, int32_t w, int64_t wdeg, const BfsArgs& a, int set,
+                                           int64_t* bin_n) {
+  if (!__ballot_sync(FULL, disc)) return;
+  const int b = disc ? bin_of(a, wdeg) : -1;
+#pragma unroll
+  for (int k = 0; k < NBINS; ++k) {
+    const unsigned mk = __ballot_sync(FULL, b == k);
+    if (!mk) continue;
+    if (sq.cnt[k] + __popc(mk) > STG) stage_flush(sq, k, a, set, bin_n);
+    if (b == k) sq.buf[k * STG + sq.cnt[k] + __popc(mk & lanemask_lt())] = w;
+    sq.cnt[k] += __popc(mk);
+  }
+  __syncwarp();
 }
 
 // One frontier edge (v -> w) of a top-down step; packed = (L+1) << 32 | v.
@@ -130,8 +179,8 @@ __device__ __forceinline__ void block_commit(const BfsArgs& a, int64_t n_found, 
 // lane offset `first`; all lanes of the warp take part in every step.
 __device__ __forceinline__ void td_edges(const BfsArgs& a, uint32_t* vis, int nxt, int32_t v, uint64_t hi,
                                          int64_t s, int64_t e, int64_t first, int64_t stride, int64_t& nf,
-                                         int64_t& mf) {
-  const uint64_t packed = hi | (uint32_t)v;
+                                         int64_t& mf, StageQ& sq) {
+  const uint64_t packed = hi | orig_of(a, v);
   for (int64_t k0 = s + first; k0 < e; k0 += stride) {
     const int64_t k = k0 + (threadIdx.x & 31);
     bool disc = false;
@@ -146,7 +195,7 @@ __device__ __forceinline__ void td_edges(const BfsArgs& a, uint32_t* vis, int nx
         mf += wd;
       }
     }
-    warp_enqueue(disc, w, wd, a, nxt, a.ctl->next_bin_n);
+    stage_push(sq, disc, w, wd, a, nxt, a.ctl->next_bin_n);
   }
 }
 
@@ -167,8 +216,13 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) bfs_td(BfsArgs a) {
   __shared__ int64_t s_beg[TD_WIN];
   __shared__ int32_t s_v[TD_WIN];
   __shared__ int64_t s_wsum[WARPS];
+  __shared__ int32_t s_stage[WARPS][NBINS * STG];
   BfsCtl* ctl = a.ctl;
   const int cur = ctl->cur, nxt = cur ^ 1;
+  StageQ sq;
+  sq.buf = s_stage[threadIdx.x >> 5];
+#pragma unroll
+  for (int k = 0; k < NBINS; ++k) sq.cnt[k] = 0;
   uint32_t* vis = ctl->vcur ? a.vis1 : a.vis0;
   const uint64_t hi = (uint64_t)(uint32_t)(ctl->level + 1) << 32;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -190,7 +244,7 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) bfs_td(BfsArgs a) {
           const int32_t v = q[ws + t];
           const int64_t b = a.row[v];
           d4[k] = a.row[v + 1] - b;
-          s_v[t] = v;
+          s_v[t] = (int32_t)orig_of(a, v);
           s_beg[t] = b;
           if (blockIdx.x == 0) atomicOr(&vis[v >> 5], 1u << (v & 31));
         }
@@ -231,7 +285,7 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) bfs_td(BfsArgs a) {
             mf += wd;
           }
         }
-        warp_enqueue(disc, w, wd, a, nxt, ctl->next_bin_n);
+        stage_push(sq, disc, w, wd, a, nxt, ctl->next_bin_n);
       }
       __syncthreads();
     }
@@ -247,7 +301,7 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) bfs_td(BfsArgs a) {
         atomicOr(&vis[v >> 5], 1u << (v & 31));
         examined += e - s;
       }
-      td_edges(a, vis, nxt, v, hi, s, e, (int64_t)wib * 32, (int64_t)WARPS * 32, nf, mf);
+      td_edges(a, vis, nxt, v, hi, s, e, (int64_t)wib * 32, (int64_t)WARPS * 32, nf, mf, sq);
     }
   }
   // bin 1: a warp per vertex
@@ -261,7 +315,7 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) bfs_td(BfsArgs a) {
         atomicOr(&vis[v >> 5], 1u << (v & 31));
         examined += e - s;
       }
-      td_edges(a, vis, nxt, v, hi, s, e, 0, 32, nf, mf);
+      td_edges(a, vis, nxt, v, hi, s, e, 0, 32, nf, mf, sq);
     }
   }
   // bin 0: edges of 32 vertices packed across the warp's lanes
@@ -270,12 +324,13 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) bfs_td(BfsArgs a) {
     const int64_t nb = ctl->bin_n[0];
     for (int64_t base = gw * 32; base < nb; base += nw * 32) {
       const int64_t i = base + lane;
-      int32_t v = -1;
+      int32_t v = -1, vo = -1;
       int64_t rs = 0, re = 0;
       if (i < nb) {
         v = q[i];
         rs = a.row[v];
         re = a.row[v + 1];
+        vo = (int32_t)orig_of(a, v);
         atomicOr(&vis[v >> 5], 1u << (v & 31));
       }
       const int32_t sd = (int32_t)(re - rs);
@@ -291,7 +346,7 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) bfs_td(BfsArgs a) {
           const int cand = owner + step;
           if (__shfl_sync(FULL, excl, cand) <= idx) owner = cand;
         }
-        const int32_t ov = __shfl_sync(FULL, v, owner);
+        const int32_t ov = __shfl_sync(FULL, vo, owner);
         const int64_t ors = __shfl_sync(FULL, rs, owner);
         const int32_t oex = __shfl_sync(FULL, excl, owner);
         bool disc = false;
@@ -306,10 +361,12 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) bfs_td(BfsArgs a) {
             mf += wd;
           }
         }
-        warp_enqueue(disc, w, wd, a, nxt, ctl->next_bin_n);
+        stage_push(sq, disc, w, wd, a, nxt, ctl->next_bin_n);
       }
     }
   }
+#pragma unroll
+  for (int k = 0; k < NBINS; ++k) stage_flush(sq, k, a, nxt, ctl->next_bin_n);
   block_commit(a, nf, mf, examined);
 }
 
@@ -401,6 +458,30 @@ __device__ __forceinline__ bool visited_bit(const uint32_t* __restrict__ vc, int
   return (__ldg(&vc[u >> 5]) >> (u & 31)) & 1u;
 }
 
+// Sparse-frontier variant: right after a top-down step the frontier is still in the queue;
+// when it is small, every CTA copies it into a shared-memory hash set (open addressing,
+// load <= 3/8) and the scan probes that set instead of the L2-resident bitmap. For an
+// unvisited vertex both tests agree: its visited neighbours are exactly its frontier ones.
+constexpr int HASH_SLOTS = 16384;
+constexpr int HASH_CAP = 6144;
+
+__device__ __forceinline__ uint32_t hash_slot(int32_t u) { return ((uint32_t)u * 2654435761u) >> 18; }
+
+__device__ __forceinline__ bool hash_has(const int32_t* __restrict__ h, int32_t u) {
+  for (uint32_t s = hash_slot(u);; s = (s + 1) & (HASH_SLOTS - 1)) {
+    const int32_t x = h[s];
+    if (x == u) return true;
+    if (x < 0) return false;
+  }
+}
+
+template <bool HASH>
+__device__ __forceinline__ bool in_frontier(const uint32_t* __restrict__ vc, const int32_t* __restrict__ h,
+                                            int32_t u) {
+  if (HASH) return hash_has(h, u);
+  return visited_bit(vc, u);
+}
+
 // Scan: a warp takes 32 x BU_V consecutive listed vertices; each lane issues the row and
 // first-neighbour loads of its BU_V vertices together, then checks up to bu_thread_scan
 // neighbours per vertex alone, in ascending order, stopping at the first visited one.
@@ -409,10 +490,26 @@ __device__ __forceinline__ bool visited_bit(const uint32_t* __restrict__ vc, int
 // (one atomic per distinct word); counts are committed once per CTA. The frontier
 // queue is not written here: the next bottom-up step reads the bitmap, and a top-down
 // step rebuilds the queue from the bitmaps first.
+template <bool HASH>
 __global__ void __launch_bounds__(BFS_THREADS, 4) bfs_bu_scan(BfsArgs a) {
+  extern __shared__ int32_t s_hash[];
   BfsCtl* ctl = a.ctl;
   const uint32_t* __restrict__ vc = ctl->vcur ? a.vis1 : a.vis0;
   uint32_t* vn = ctl->vcur ? a.vis0 : a.vis1;
+  if (HASH) {
+    for (int i = threadIdx.x; i < HASH_SLOTS; i += BFS_THREADS) s_hash[i] = -1;
+    __syncthreads();
+    for (int b = 0; b < NBINS; ++b) {
+      const int32_t* q = queue_of(a, ctl->cur, b);
+      const int64_t nb = ctl->bin_n[b];
+      for (int64_t i = threadIdx.x; i < nb; i += BFS_THREADS) {
+        const int32_t u = q[i];
+        for (uint32_t sl = hash_slot(u);; sl = (sl + 1) & (HASH_SLOTS - 1))
+          if (atomicCAS(&s_hash[sl], -1, u) == -1) break;
+      }
+    }
+    __syncthreads();
+  }
   const uint64_t hi = (uint64_t)(uint32_t)(ctl->level + 1) << 32;
   const int64_t nu = ctl->ulist_n;
   const int lane = threadIdx.x & 31;
@@ -457,14 +554,24 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) bfs_bu_scan(BfsArgs a) {
         }
       }
       if (!any) break;
-      uint32_t vw[BU_V];
+      if (HASH) {
 #pragma unroll
-      for (int j = 0; j < BU_V; ++j) vw[j] = u[j] >= 0 ? __ldg(&vc[u[j] >> 5]) : 0u;
+        for (int j = 0; j < BU_V; ++j) {
+          if (u[j] >= 0) {
+            ++nx[j];
+            if (hash_has(s_hash, u[j])) par[j] = u[j];
+          }
+        }
+      } else {
+        uint32_t vw[BU_V];
 #pragma unroll
-      for (int j = 0; j < BU_V; ++j) {
-        if (u[j] >= 0) {
-          ++nx[j];
-          if ((vw[j] >> (u[j] & 31)) & 1u) par[j] = u[j];
+        for (int j = 0; j < BU_V; ++j) vw[j] = u[j] >= 0 ? __ldg(&vc[u[j] >> 5]) : 0u;
+#pragma unroll
+        for (int j = 0; j < BU_V; ++j) {
+          if (u[j] >= 0) {
+            ++nx[j];
+            if ((vw[j] >> (u[j] & 31)) & 1u) par[j] = u[j];
+          }
         }
       }
     }
@@ -474,7 +581,7 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) bfs_bu_scan(BfsArgs a) {
     for (int j = 0; j < BU_V; ++j) {
       const bool fnd = par[j] >= 0;
       if (fnd) {
-        a.state[w[j]] = hi | (uint32_t)par[j];
+        a.state[w[j]] = hi | orig_of(a, par[j]);
         ++nf;
         mf += e[j] - s[j];
       }
@@ -495,7 +602,7 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) bfs_bu_scan(BfsArgs a) {
           bool hit = false;
           if (k2 < e2) {
             u = a.col[k2];
-            hit = visited_bit(vc, u);
+            hit = in_frontier<HASH>(vc, s_hash, u);
           }
           const unsigned hm = __ballot_sync(FULL, hit);
           if (lane == 0) examined += hm ? __ffs(hm) : min((int64_t)32, e2 - b0);
@@ -505,7 +612,7 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) bfs_bu_scan(BfsArgs a) {
           }
         }
         if (par2 >= 0 && lane == 0) {
-          a.state[w2] = hi | (uint32_t)par2;
+          a.state[w2] = hi | orig_of(a, par2);
           atomicOr(&vn[w2 >> 5], 1u << (w2 & 31));
           ++nf;
           mf += d2;
@@ -567,16 +674,17 @@ __global__ void bfs_decide(BfsArgs a, cudaGraphConditionalHandle h_loop, int use
     }
     c->need_mark = (dir == DIR_TD && nd == DIR_BU);
     c->need_queue = (dir == DIR_BU && nd == DIR_TD);
+    c->bu_hash = c->need_mark && nn <= HASH_CAP;
     c->dir = nd;
   }
   if (use_handles) cudaGraphSetConditional(h_loop, c->done ? 0u : 1u);
 }
 
 // Which step kernels run next: 0 top-down, 1 bottom-up, 2 mark + bottom-up,
-// 3 queue rebuild + top-down.
+// 3 queue rebuild + top-down, 4 mark + bottom-up probing a shared-memory frontier set.
 __device__ __forceinline__ unsigned step_kind(const BfsCtl* c) {
   if (c->dir == DIR_TD) return c->need_queue ? 3u : 0u;
-  return c->need_mark ? 2u : 1u;
+  return c->need_mark ? (c->bu_hash ? 4u : 2u) : 1u;
 }
 
 // First node of each loop iteration: routes the switch to the step now due.
@@ -617,6 +725,7 @@ __device__ void ctl_begin(const BfsArgs& a, int32_t start, int32_t start_level, 
   c->examined = 0;
   c->ulist_n = 0;
   c->need_queue = 0;
+  c->bu_hash = 0;
   c->alpha = alpha;
   c->beta = beta;
   c->force = force;
@@ -635,7 +744,7 @@ __device__ void ctl_begin(const BfsArgs& a, int32_t start, int32_t start_level, 
   }
   c->done = 0;
   const int64_t d = a.row[start + 1] - a.row[start];
-  a.state[start] = ((uint64_t)(uint32_t)start_level << 32) | (uint32_t)start;
+  a.state[start] = ((uint64_t)(uint32_t)start_level << 32) | orig_of(a, start);
   a.vis0[start >> 5] |= 1u << (start & 31);
   const int b = bin_of(a, d);
   queue_of(a, 0, b)[0] = start;
@@ -682,7 +791,7 @@ __global__ void et_start(BfsArgs a, EtArgs e, int32_t root, int32_t alpha, int32
 }
 
 // Levels and parents of every vertex in vertex-id order: core vertices from the core
-// BFS state (parents back to vertex ids), edge-tree vertices hanging from a core vertex
+// BFS state (parents already vertex ids), edge-tree vertices hanging from a core vertex
 // from that vertex's level (Alg. 7 / Alg. 10 with levels), tree vertices hanging from a
 // tree vertex -2 ("resolve pending", see et_resolve), everything else -1.
 // Four consecutive vertices per thread: one 128-bit vinfo load, four independent state
@@ -717,7 +826,7 @@ __global__ void et_output(EtArgs e, const uint64_t* __restrict__ state, int32_t*
       p[k] = l[k];
       if (st[k] != UNVISITED) {
         l[k] = (int32_t)(st[k] >> 32) + add[k];
-        p[k] = e.new2old[add[k] ? cid[k] : (int32_t)(uint32_t)st[k]];
+        p[k] = add[k] ? e.new2old[cid[k]] : (int32_t)(uint32_t)st[k];
       }
     }
     reinterpret_cast<int4*>(level)[i] = make_int4(l[0], l[1], l[2], l[3]);
@@ -732,7 +841,7 @@ __global__ void et_output(EtArgs e, const uint64_t* __restrict__ state, int32_t*
       const uint64_t st = state[cid];
       if (st != UNVISITED) {
         l = (int32_t)(st >> 32) + add;
-        p = e.new2old[add ? cid : (int32_t)(uint32_t)st];
+        p = add ? e.new2old[cid] : (int32_t)(uint32_t)st;
       }
     }
     level[v] = l;
@@ -793,17 +902,36 @@ int grid_stream(const gt_graph* g, int64_t work) {
   return (int)std::max<int64_t>(1, std::min(want, cap));
 }
 
+constexpr int NKINDS = 5;
+constexpr size_t HASH_SMEM = sizeof(int32_t) * HASH_SLOTS;
+
+// Lets the shared-memory-set variant of the scan take its 64 KB of dynamic shared memory.
+int prepare_kernels() {
+  return cuda_fail(cudaFuncSetAttribute(bfs_bu_scan<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)HASH_SMEM),
+                   "scan shared memory");
+}
+
 // The step kernels of one level: 0 top-down, 1 bottom-up (gather + scan), 2 mark +
-// bottom-up, 3 queue rebuild + top-down.
+// bottom-up, 3 queue rebuild + top-down, 4 mark + bottom-up with the frontier set in
+// shared memory.
 void launch_step(int kind, const BfsArgs& a, int grid, cudaStream_t s) {
   if (kind == 3) bfs_queue_from_bitmap<<<grid, BFS_THREADS, 0, s>>>(a);
   if (kind == 0 || kind == 3) {
     bfs_td<<<grid, BFS_THREADS, 0, s>>>(a);
     return;
   }
-  if (kind == 2) bfs_mark<<<grid, BFS_THREADS, 0, s>>>(a);
+  if (kind == 2 || kind == 4) bfs_mark<<<grid, BFS_THREADS, 0, s>>>(a);
   bfs_bu_gather<<<grid, BFS_THREADS, 0, s>>>(a);
-  bfs_bu_scan<<<grid, BFS_THREADS, 0, s>>>(a);
+  if (kind == 4)
+    bfs_bu_scan<true><<<grid, BFS_THREADS, HASH_SMEM, s>>>(a);
+  else
+    bfs_bu_scan<false><<<grid, BFS_THREADS, 0, s>>>(a);
+}
+
+unsigned host_step_kind(int dir, int need_mark, int need_queue, int bu_hash) {
+  if (dir == DIR_TD) return need_queue ? 3u : 0u;
+  return need_mark ? (bu_hash ? 4u : 2u) : 1u;
 }
 
 // Builds the CUDA graph of the level loop for one view:
@@ -847,19 +975,20 @@ int build_loop_graph(gt_graph* g, const View& v, cudaGraphExec_t* out) {
     kp.kernelParams = args;
     fail(cudaGraphAddKernelNode(&sel, body, nullptr, 0, &kp), "select node");
   }
-  cudaGraph_t branch[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaGraph_t branch[NKINDS] = {};
   cudaGraphNode_t sw = nullptr;
+  if (rc == GT_OK) rc = prepare_kernels();
   if (rc == GT_OK) {
     cudaGraphNodeParams np{};
     np.type = cudaGraphNodeTypeConditional;
     np.conditional.handle = h_dir;
     np.conditional.type = cudaGraphCondTypeSwitch;
-    np.conditional.size = 4;
+    np.conditional.size = NKINDS;
     fail(cudaGraphAddNode(&sw, body, &sel, nullptr, 1, &np), "switch node");
     if (rc == GT_OK)
-      for (int i = 0; i < 4; ++i) branch[i] = np.conditional.phGraph_out[i];
+      for (int i = 0; i < NKINDS; ++i) branch[i] = np.conditional.phGraph_out[i];
   }
-  for (int i = 0; i < 4 && rc == GT_OK; ++i) {
+  for (int i = 0; i < NKINDS && rc == GT_OK; ++i) {
     fail(cudaStreamBeginCaptureToGraph(cs, branch[i], nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed), "capture");
     if (rc != GT_OK) break;
     launch_step(i, a, grid, cs);
@@ -898,11 +1027,13 @@ int run_level_loop(gt_graph* g, View& v, int which, cudaStream_t s) {
   const BfsArgs a = make_args(v, t);
   const int grid = g->launch.grid;
   struct Head {
-    int32_t level, dir, done, cur, vcur, need_mark, need_queue;
+    int32_t level, dir, done, cur, vcur, need_mark, need_queue, bu_hash;
   } h{};
   const cudaGraphConditionalHandle none = 0;
   int timed_steps = 0;
   g->step_ms.clear();
+  int rc0 = prepare_kernels();
+  if (rc0 != GT_OK) return rc0;
   for (int guard = 0; guard < (1 << 30); ++guard) {
     int rc = cuda_fail(cudaMemcpyAsync(&h, v.ctl, sizeof(h), cudaMemcpyDeviceToHost, s), "ctl readback");
     if (rc == GT_OK) rc = cuda_fail(cudaStreamSynchronize(s), "level sync");
@@ -918,7 +1049,7 @@ int run_level_loop(gt_graph* g, View& v, int which, cudaStream_t s) {
       }
       cudaEventRecord(g->step_events[2 * guard], s);
     }
-    launch_step(h.dir == DIR_TD ? (h.need_queue ? 3 : 0) : (h.need_mark ? 2 : 1), a, grid, s);
+    launch_step((int)host_step_kind(h.dir, h.need_mark, h.need_queue, h.bu_hash), a, grid, s);
     if (timed) {
       cudaEventRecord(g->step_events[2 * guard + 1], s);
       ++timed_steps;

@@ -558,6 +558,7 @@ int build_graph(gt_graph* g, const int64_t* edges, int64_t m, int64_t n, cudaStr
   TRY(tmp_malloc(tmp, (void**)&cdeg, sizeof(int32_t) * std::max<int64_t>(nc, 1)));
   View& cv = g->core;
   cv.n = nc;
+  cv.new2old = g->new2old;
   TRY(device_malloc(g, (void**)&cv.row, sizeof(int64_t) * (nc + 1)));
   const int gw = grid_for(g, nc * 32);
   if (nc > 0) core_degree<<<gw, BT, 0, s>>>(g->row, g->col, is_core, g->new2old, nc, cdeg);

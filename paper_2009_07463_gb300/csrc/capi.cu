@@ -49,6 +49,18 @@ int where(const void* p) {
   return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? 1 : 0;
 }
 
+// Device address of page-locked host memory mapped into the device's address space, or
+// null for pageable or unmapped memory.
+int32_t* mapped_host(void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+  return (int32_t*)a.devicePointer;
+}
+
 void apply_launch(gt_graph* g) {
   int bpm = g->tuning.blocks_per_sm > 0 ? g->tuning.blocks_per_sm : 8;
   g->launch.grid = g->launch.sms * bpm;
@@ -92,6 +104,15 @@ int bfs_common(gt_graph_t g, bool et, int64_t root, int32_t* parent, int32_t* le
   }
   gt::View& v = et ? g->core : g->plain;
   if (wp == 1) return run_bfs(g, v, et, root, parent, level, s);
+  // Pinned (page-locked, device-mapped) host buffers: the output pass writes them directly
+  // over the host link, so no device staging or copy is needed.
+  int32_t* mp = mapped_host(parent);
+  int32_t* ml = mapped_host(level);
+  if (mp && ml) {
+    rc = run_bfs(g, v, et, root, mp, ml, s);
+    if (!rc) rc = cuda_fail(cudaStreamSynchronize(s), "bfs sync");
+    return rc;
+  }
   if (!g->scratch_out) {
     rc = device_malloc(g, (void**)&g->scratch_out, sizeof(int32_t) * 2 * g->n);
     if (rc) return rc;
@@ -130,7 +151,7 @@ GT_API void gt_config_default(gt_config* c) {
 GT_API void gt_tuning_default(gt_tuning* t) {
   if (!t) return;
   memset(t, 0, sizeof(*t));
-  t->alpha = 64;
+  t->alpha = 32;
   t->beta = 256;
   t->td_warp_min = 32;
   t->td_cta_min = 256;

@@ -32,6 +32,7 @@ struct BfsCtl {
   int32_t vcur;       // visited bitmap that is current (0/1)
   int32_t need_mark;  // 1: set visited bits of the current queue before a bottom-up step
   int32_t need_queue; // 1: rebuild the current queue from the bitmaps before a top-down step
+  int32_t bu_hash;    // 1: the bottom-up step may probe a shared-memory copy of the frontier
   int32_t nlevels;    // steps taken
   int64_t n_f;        // current frontier vertices
   int64_t m_f;        // their summed degree
@@ -62,6 +63,7 @@ struct View {
   uint32_t* vis[2] = {nullptr, nullptr};
   int32_t* queues = nullptr;   // 2 x NBINS queues of n entries: [set][bin][n]
   int32_t* ulist = nullptr;    // bottom-up: ascending list of unvisited vertices
+  const int32_t* new2old = nullptr;  // view id -> vertex id (core view); null when ids agree
   BfsCtl* ctl = nullptr;
 };
 

@@ -52,7 +52,7 @@ def test_struct_layouts_match_header(tmp_path):
 def test_defaults_and_errors_without_gpu():
     L = gt.lib()
     t = gt.tuning_default()
-    assert (t.alpha, t.beta, t.td_warp_min, t.launch_mode, t.batch_alpha) == (64, 256, 32, 0, 14)
+    assert (t.alpha, t.beta, t.td_warp_min, t.launch_mode, t.batch_alpha) == (32, 256, 32, 0, 14)
     assert L.gt_strerror(-1) == b"invalid argument"
     # argument checks fail before any device work
     h = ctypes.c_void_p()
