@@ -61,6 +61,8 @@ def parse():
                          "on scale 24 plus a mixed 32-graph batch; serve: Poisson queries on 12 resident graphs")
     ap.add_argument("--serve-rates", default="4000,16000,48000")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-policies", default="adaptive,batched,single",
+                    help="server dispatch policies to run on each arrival schedule (the first is the headline)")
     return ap.parse_args()
 
 
@@ -520,7 +522,7 @@ def _make_graph(gt, graphgen, torch, kind, a_, seed, dev):
 
 
 def run_batch_workload(a, rank, local):
-    """Config 4: 64 roots in one lane word on R-MAT scale 24, and a mixed batch of 32 graphs
+    """Batch workload: 64 roots in one lane word on R-MAT scale 24, and a mixed batch of 32 graphs
     (R-MAT scales 14-22, uniform graphs of average degree 16), 64 roots each, every batch in
     one persistent launch with autotuned parameters; against the same roots run one at a
     time with gt_bfs. Queries/s and GTEPS-equivalent (traversed tuples / time)."""
@@ -595,13 +597,59 @@ def run_batch_workload(a, rank, local):
     print(json.dumps(out), flush=True)
 
 
-def run_serve_workload(a, rank, local):
-    """Config 5: 12 resident graphs (R-MAT scales 18-25 at edge factor 16; uniform graphs of
-    average degree 8-32), a 48 GiB HBM budget, Poisson arrivals of single-root queries at
-    each stated rate (roots uniform over vertices of degree >= 1 of a uniformly chosen
-    graph). Served with continuous batching vs the same arrival schedule run by one worker
-    with sequential gt_bfs calls. Queries/s and p50/p99 latency (arrival -> results ready)."""
+def _serve_once(gt, graphs, bufs, RING, nq, gaps, gsel, roots, policy):
+    """One arrival schedule through a server with the given dispatch policy."""
     import threading
+    srv = gt.Server(hbm_budget_bytes=48 << 30, streams=2, max_batch_roots=128, window_us=100, policy=policy)
+    gids = [srv.add_graph(g) for g in graphs]
+    slot_busy = [[None] * RING for _ in graphs]
+    ring_pos = [0] * len(graphs)
+    lat = [0.0] * nq
+    t_arr = [0.0] * nq
+    tickets = [None] * nq
+    done_ev = threading.Event()
+
+    def collector():
+        for j in range(nq):
+            while tickets[j] is None:
+                time.sleep(0.00005)
+            srv.poll(tickets[j], 60000)
+            lat[j] = time.perf_counter() - t_arr[j]
+        done_ev.set()
+    col = threading.Thread(target=collector)
+    col.start()
+    t0 = time.perf_counter()
+    t_next = t0
+    for j in range(nq):
+        t_next += gaps[j]
+        while time.perf_counter() < t_next:
+            pass
+        gi = int(gsel[j])
+        k = ring_pos[gi]
+        ring_pos[gi] = (k + 1) % RING
+        prev = slot_busy[gi][k]
+        if prev is not None:
+            while lat[prev] == 0.0:  # ring buffer still owned by an earlier query
+                time.sleep(0.00002)
+        slot_busy[gi][k] = j
+        t_arr[j] = t_next
+        p, l = bufs[gi][k]
+        tickets[j] = srv.submit(gids[gi], roots[j], p, l)
+    done_ev.wait()
+    st = srv.stats()  # latency stamped by the completion callback: submit -> results ready
+    srv.destroy()
+    col.join()
+    return {"qps": round(st["qps"], 1), "p50_us": round(st["p50_us"], 1), "p99_us": round(st["p99_us"], 1),
+            "batched_launches": st["batches"]}
+
+
+def run_serve_workload(a, rank, local):
+    """Serving workload: 12 resident graphs (R-MAT scales 18-25 at edge factor 16; uniform
+    graphs of 2^20 vertices and average degree 8-32), a 48 GiB HBM budget, Poisson arrivals
+    of single-root queries at each stated rate (roots uniform over vertices of degree >= 1
+    of a uniformly chosen graph). Served under each dispatch policy vs the same arrival
+    schedule run by one worker with sequential gt_bfs calls. Queries/s and p50/p99 latency
+    (arrival -> results ready)."""
     import numpy as np
     import torch
 
@@ -630,48 +678,11 @@ def run_serve_workload(a, rank, local):
         gaps = rng.exponential(1.0 / rate, size=nq)
         gsel = rng.integers(0, len(graphs), size=nq)
         roots = [int(cand[gi][rng.integers(0, cand[gi].size)]) for gi in gsel]
-        # served
-        srv = gt.Server(hbm_budget_bytes=48 << 30, streams=2, max_batch_roots=128, window_us=100)
-        gids = [srv.add_graph(g) for g in graphs]
-        slot_busy = [[None] * RING for _ in graphs]
-        ring_pos = [0] * len(graphs)
-        lat = [0.0] * nq
-        t_arr = [0.0] * nq
-        tickets = [None] * nq
-        done_ev = threading.Event()
-
-        def collector():
-            for j in range(nq):
-                while tickets[j] is None:
-                    time.sleep(0.00005)
-                srv.poll(tickets[j], 60000)
-                lat[j] = time.perf_counter() - t_arr[j]
-            done_ev.set()
-        col = threading.Thread(target=collector)
-        col.start()
-        t0 = time.perf_counter()
-        t_next = t0
-        for j in range(nq):
-            t_next += gaps[j]
-            while time.perf_counter() < t_next:
-                pass
-            gi = int(gsel[j])
-            k = ring_pos[gi]
-            ring_pos[gi] = (k + 1) % RING
-            prev = slot_busy[gi][k]
-            if prev is not None:
-                while lat[prev] == 0.0:  # ring buffer still owned by an earlier query
-                    time.sleep(0.00002)
-            slot_busy[gi][k] = j
-            t_arr[j] = t_next
-            p, l = bufs[gi][k]
-            tickets[j] = srv.submit(gids[gi], roots[j], p, l)
-        done_ev.wait()
-        st = srv.stats()  # latency stamped by the completion callback: submit -> results ready
-        srv.destroy()
-        col.join()
-        served = {"qps": round(st["qps"], 1), "p50_us": round(st["p50_us"], 1), "p99_us": round(st["p99_us"], 1),
-                  "batches": st["batches"], "mean_batch": round(nq / max(st["batches"], 1), 1)}
+        served = {}
+        for pol in [x for x in a.serve_policies.split(",") if x]:
+            served[pol] = _serve_once(gt, graphs, bufs, RING, nq, gaps, gsel, roots,
+                                      {"adaptive": gt.GT_SERVE_ADAPTIVE, "batched": gt.GT_SERVE_BATCHED,
+                                       "single": gt.GT_SERVE_SINGLE}[pol])
         # sequential single-root calls on the same schedule (one worker, FIFO)
         lat2 = []
         stream = torch.cuda.current_stream()
@@ -693,9 +704,10 @@ def run_serve_workload(a, rank, local):
         seq = {"qps": round(nq / (t_end2 - t0), 1), "p50_us": round(1e6 * lat2s[nq // 2], 1),
                "p99_us": round(1e6 * lat2s[min(nq - 1, int(0.99 * nq))], 1)}
         results.append({"rate_qps": rate, "queries": nq, "served": served, "sequential": seq})
-    best = max(results, key=lambda r: r["served"]["qps"])
-    out = {"metric": "served BFS queries/s and p99 latency (continuous batching)", "value": best["served"]["qps"],
-           "unit": "queries/s", "p99_us": best["served"]["p99_us"], "n_gpus": 1, "higher_is_better": True,
+    head = [x for x in a.serve_policies.split(",") if x][0]
+    best = max(results, key=lambda r: r["served"][head]["qps"])
+    out = {"metric": "served BFS queries/s and p99 latency (continuous batching)", "value": best["served"][head]["qps"],
+           "unit": "queries/s", "p99_us": best["served"][head]["p99_us"], "policy": head, "n_gpus": 1, "higher_is_better": True,
            "dtype": "int32", "data": "synthetic",
            "config": {"workload": "serve: 12 resident graphs (rmat s18-25 ef16, uniform 2^20 deg 8/16/24/32), "
                                   "Poisson arrivals", "hbm_budget_gib": 48, "streams": 2, "max_batch_roots": 128,

@@ -177,21 +177,28 @@ GT_API int gt_count_traversed(const int64_t* edges, int64_t m, const int32_t* le
                               void* stream);
 
 /* ---- Serving: continuous batching over resident graphs (no counterpart in the paper) ----
- * A server keeps graph handles resident, queues single-root queries per graph, and a
- * scheduler thread turns the pending roots of a graph into batched launches (64 roots per
- * lane word, as gt_bfs_batch) whenever one of its streams is free: at once when the GPU
- * is idle, otherwise after up to window_us to fill lane words. Queries that arrive while
- * batches run join the next batch, which runs beside those in flight (each stream's
- * launch takes 1/streams of the SMs). Each result equals gt_bfs from that root. */
+ * A server keeps graph handles resident and queues single-root queries per graph. A
+ * scheduler thread dispatches the pending roots of a graph, whenever one of its streams is
+ * free, in the form its running per-graph cost estimates say is cheaper: up to 64
+ * single-root traversals back to back (one such flight per graph at a time), or one
+ * batched launch (64 roots per lane word, as gt_bfs_batch) whose cost hardly depends on
+ * how many lanes are filled. A batched launch goes at once when the GPU is idle,
+ * otherwise after up to window_us to fill lane words (only where batching pays). Flights
+ * on different streams overlap on the device. Each result equals gt_bfs from that root.
+ * While a graph is added to a running server, the caller must not traverse it through
+ * gt_bfs, gt_bfs_plain, gt_bfs_trace or gt_autotune: those share its traversal state. */
 typedef struct gt_serve_config {
   int64_t hbm_budget_bytes; /* graphs + batch storage admitted up to this (default 48 GiB) */
-  int32_t streams;          /* batches in flight at once (default 2) */
+  int32_t streams;          /* flights (batched or single-root) at once (default 2) */
   int32_t max_batch_roots;  /* roots per launch (default 256) */
   double window_us;         /* wait to fill lane words while other batches run (default 200) */
+  int32_t policy;           /* GT_SERVE_ADAPTIVE (default), GT_SERVE_BATCHED or GT_SERVE_SINGLE */
 } gt_serve_config;
 
+enum { GT_SERVE_ADAPTIVE = 0, GT_SERVE_BATCHED = 1, GT_SERVE_SINGLE = 2 };
+
 typedef struct gt_serve_stats {
-  int64_t submitted, completed, failed, batches, inflight, pending;
+  int64_t submitted, completed, failed, batches, inflight, pending; /* batches: batched launches */
   double p50_us, p99_us, mean_us, max_us; /* submit -> results in the caller's buffers */
   double qps;                             /* completed / (last completion - first submit) */
   int64_t device_bytes;                   /* graphs + batch storage held against the budget */

@@ -16,6 +16,7 @@ import numpy as np
 from . import native
 
 GT_OK, GT_EINVAL, GT_ENOMEM, GT_ETIMEOUT, GT_EBUSY, GT_EDEVICE, GT_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+GT_SERVE_ADAPTIVE, GT_SERVE_BATCHED, GT_SERVE_SINGLE = 0, 1, 2
 CORE_INTERNAL, CORE_EDGE, TREE_INTERNAL, TREE_LEAF, VERTEX_ZERO = 0, 1, 2, 3, 4
 
 
@@ -43,7 +44,7 @@ class gt_level_info(ctypes.Structure):
 
 class gt_serve_config(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("streams", ctypes.c_int32), ("max_batch_roots", ctypes.c_int32),
-                ("window_us", ctypes.c_double)]
+                ("window_us", ctypes.c_double), ("policy", ctypes.c_int32)]
 
 
 class gt_serve_stats(ctypes.Structure):
@@ -307,7 +308,8 @@ class Server:
     """Continuous-batching BFS server over resident graphs (gt_serve_*)."""
 
     def __init__(self, hbm_budget_bytes: int | None = None, streams: int | None = None,
-                 max_batch_roots: int | None = None, window_us: float | None = None):
+                 max_batch_roots: int | None = None, window_us: float | None = None,
+                 policy: int | None = None):
         cfg = gt_serve_config()
         lib().gt_serve_config_default(ctypes.byref(cfg))
         if hbm_budget_bytes is not None:
@@ -318,6 +320,8 @@ class Server:
             cfg.max_batch_roots = int(max_batch_roots)
         if window_us is not None:
             cfg.window_us = float(window_us)
+        if policy is not None:
+            cfg.policy = int(policy)
         h = ctypes.c_void_p()
         _check(lib().gt_serve_create(ctypes.byref(cfg), ctypes.byref(h)), "gt_serve_create")
         self._h = h.value

@@ -1,12 +1,16 @@
 // serve.cu -- continuous-batching BFS server over resident graphs.
 //
-// Queries (graph, root, caller-owned device outputs) are queued per graph. A scheduler
-// thread turns the pending roots of one graph into a batched launch (64 roots per lane
-// word, see batch.cu) whenever one of the server's streams is free: it dispatches at
-// once when the GPU is idle, otherwise it waits up to `window_us` to fill lane words.
-// Queries that arrive while batches are on the GPU join the next batch, which runs
-// beside the ones in flight (each stream's cooperative launch takes 1/streams of the
-// SMs), so their work overlaps on the device. Graphs are admitted against an HBM budget
+// Queries (graph, root, caller-owned device outputs) are queued per graph. Whenever one of
+// the server's streams is free, a scheduler thread dispatches the pending roots of the
+// graph with the oldest query in one of two forms, whichever its running estimates say
+// is cheaper: up to 64 single-root edge-tree traversals back to back on the stream (each
+// query completes on its own), or one batched launch (64 roots per lane word, batch.cu)
+// whose cost hardly depends on how many lanes are filled. A graph runs at most one
+// single-root flight at a time (the traversal state is the graph's own). A batched
+// launch is dispatched at once when the GPU is idle; otherwise, if batching pays on that
+// graph, the scheduler waits up to `window_us` to fill lane words. Flights on different
+// streams overlap on the device (a cooperative batched launch takes 1/streams of the
+// SMs). Graphs are admitted against an HBM budget
 // (graph storage + one lane word of batch storage); more lane-word storage is taken
 // while the budget allows. Completion is signalled by a host callback on the stream,
 // which stamps every query's latency (submit -> results in the caller's buffers).
@@ -53,15 +57,32 @@ struct GraphEntry {
   std::deque<Query*> pending;
   std::vector<SlotBuf> slots;  // lane-word storage owned by the server
   std::vector<int> free_slots;
+  bool single_busy = false;    // a flight is running single-root traversals on this graph
+  double est_single_us = 0;    // running estimates (0 = not measured yet): one single-root
+  double est_word_us = 0;      // traversal; one 64-root lane word in a batched launch
 };
 
+struct Flight;
+struct QueryDone {
+  Flight* f;
+  Query* q;
+};
+
+// Work on one stream: either one batched launch over `slots`, or `queries` run as
+// single-root traversals one after another (each completes on its own).
 struct Flight {
   void* srv = nullptr;
   int stream = 0;
   int gid = 0;
+  bool single = false;
+  double t_launch = 0, t_prev = 0;
+  int remaining = 0;
   std::vector<Query*> queries;
   std::vector<int> slots;
+  std::vector<QueryDone> done;
 };
+
+double ema(double old, double x) { return old > 0 ? 0.8 * old + 0.2 * x : x; }
 
 }  // namespace
 }  // namespace gt
@@ -90,6 +111,32 @@ struct gt_server {
 namespace gt {
 namespace {
 
+// Host callback after one single-root traversal of a single-mode flight.
+void CUDART_CB on_query_done(void* arg) {
+  QueryDone* d = (QueryDone*)arg;
+  Flight* f = d->f;
+  gt_server* s = (gt_server*)f->srv;
+  const double t = now_us();
+  std::lock_guard<std::mutex> lk(s->mu);
+  GraphEntry& ge = s->graphs[f->gid];
+  ge.est_single_us = ema(ge.est_single_us, t - f->t_prev);
+  f->t_prev = t;
+  Query* q = d->q;
+  q->done = true;
+  q->rc = GT_OK;
+  q->t_done = t;
+  s->lat_us.push_back(t - q->t_submit);
+  s->completed++;
+  s->t_last = t;
+  if (--f->remaining == 0) {
+    ge.single_busy = false;
+    s->flights[f->stream] = nullptr;
+    delete f;
+    s->cv_sched.notify_all();
+  }
+  s->cv_done.notify_all();
+}
+
 void CUDART_CB on_flight_done(void* arg) {
   Flight* f = (Flight*)arg;
   gt_server* s = (gt_server*)f->srv;
@@ -97,6 +144,7 @@ void CUDART_CB on_flight_done(void* arg) {
   std::lock_guard<std::mutex> lk(s->mu);
   const int rc = batch_status(&s->ctxs[f->stream]);
   GraphEntry& ge = s->graphs[f->gid];
+  if (!f->slots.empty()) ge.est_word_us = ema(ge.est_word_us, (t - f->t_launch) / f->slots.size());
   for (int k : f->slots) ge.free_slots.push_back(k);
   for (Query* q : f->queries) {
     q->done = true;
@@ -134,13 +182,14 @@ bool grow_slots(gt_server* s, GraphEntry& ge) {
   return true;
 }
 
-// Picks the graph whose oldest pending query is oldest; -1 if none. Caller holds the lock.
+// Picks the graph whose oldest pending query is oldest, among graphs without a running
+// single-root flight; -1 if none. Caller holds the lock.
 int oldest_graph(gt_server* s) {
   int best = -1;
   double t = 0;
   for (size_t i = 0; i < s->graphs.size(); ++i) {
     const GraphEntry& ge = s->graphs[i];
-    if (ge.pending.empty()) continue;
+    if (ge.pending.empty() || ge.single_busy) continue;  // a single-root flight drains it first
     if (best < 0 || ge.pending.front()->t_submit < t) {
       best = (int)i;
       t = ge.pending.front()->t_submit;
@@ -179,8 +228,66 @@ void scheduler(gt_server* s) {
     GraphEntry& ge = s->graphs[gi];
     const double age = now_us() - ge.pending.front()->t_submit;
     const size_t want = std::min<size_t>(ge.pending.size(), (size_t)s->cfg.max_batch_roots);
-    if (busy > 0 && want < 64 && age < s->cfg.window_us) {
+    // Mode: k single-root traversals cost k * est_single; a batched launch costs about
+    // est_word per 64-root lane word whatever the number of roots in it. Unmeasured modes
+    // are tried first (single for a few queries, batch for many).
+    const double words_f = (double)((want + 63) / 64);
+    bool single;
+    if (ge.est_single_us <= 0)
+      single = want <= 4 || ge.est_word_us > 0;
+    else if (ge.est_word_us <= 0)
+      single = want < 8;
+    else
+      single = want * ge.est_single_us <= words_f * ge.est_word_us;
+    if (s->cfg.policy != GT_SERVE_ADAPTIVE) single = s->cfg.policy == GT_SERVE_SINGLE;
+    const bool batching_pays = s->cfg.policy == GT_SERVE_BATCHED ||
+                               (ge.est_single_us > 0 && ge.est_word_us > 0 && 64 * ge.est_single_us > ge.est_word_us);
+    if (!single && busy > 0 && want < 64 && age < s->cfg.window_us && batching_pays) {
       s->cv_sched.wait_for(lk, std::chrono::microseconds((int64_t)std::max(1.0, s->cfg.window_us - age)));
+      continue;
+    }
+    if (single) {
+      Flight* f = new Flight();
+      f->srv = s;
+      f->stream = free_stream;
+      f->gid = gi;
+      f->single = true;
+      const size_t take = std::min<size_t>(want, 64);
+      for (size_t i = 0; i < take; ++i) {
+        f->queries.push_back(ge.pending.front());
+        ge.pending.pop_front();
+      }
+      f->done.resize(take);
+      for (size_t i = 0; i < take; ++i) f->done[i] = QueryDone{f, f->queries[i]};
+      f->remaining = (int)take;
+      f->t_launch = f->t_prev = now_us();
+      ge.single_busy = true;
+      s->flights[free_stream] = f;
+      cudaStream_t st = s->streams[free_stream];
+      lk.unlock();  // the graph's single-root state is this flight's alone (single_busy)
+      size_t launched = 0;
+      int rc = GT_OK;
+      for (; launched < take && rc == GT_OK; ++launched) {
+        Query* q = f->queries[launched];
+        rc = run_bfs(ge.g, ge.g->core, true, q->root, q->parent, q->level, st);
+        if (rc == GT_OK) rc = cuda_fail(cudaLaunchHostFunc(st, on_query_done, &f->done[launched]), "host callback");
+      }
+      lk.lock();
+      if (rc != GT_OK) {  // queries past the failure will not call back: fail them here
+        const size_t ok = launched - 1;
+        for (size_t i = ok; i < take; ++i) {
+          f->queries[i]->done = true;
+          f->queries[i]->rc = rc;
+          s->failed++;
+        }
+        f->remaining -= (int)(take - ok);
+        if (f->remaining == 0) {
+          ge.single_busy = false;
+          s->flights[free_stream] = nullptr;
+          delete f;
+        }
+        s->cv_done.notify_all();
+      }
       continue;
     }
     const int words_needed = (int)((want + 63) / 64);
@@ -206,6 +313,7 @@ void scheduler(gt_server* s) {
     }
     s->flights[free_stream] = f;
     s->batches++;
+    f->t_launch = now_us();
     // build the launch outside the lock
     std::vector<int64_t> roots(take);
     std::vector<int32_t*> op(take), ol(take);
@@ -259,6 +367,7 @@ GT_API void gt_serve_config_default(gt_serve_config* c) {
   c->streams = 2;
   c->max_batch_roots = 256;
   c->window_us = 200.0;
+  c->policy = GT_SERVE_ADAPTIVE;
 }
 
 GT_API int gt_serve_create(const gt_serve_config* cfg, gt_server_t* out) {
@@ -271,7 +380,8 @@ GT_API int gt_serve_create(const gt_serve_config* cfg, gt_server_t* out) {
   else
     gt_serve_config_default(&s->cfg);
   if (s->cfg.streams < 1 || s->cfg.streams > 16 || s->cfg.max_batch_roots < 1 || s->cfg.max_batch_roots > 16384 ||
-      s->cfg.hbm_budget_bytes < 0 || s->cfg.window_us < 0) {
+      s->cfg.hbm_budget_bytes < 0 || s->cfg.window_us < 0 || s->cfg.policy < GT_SERVE_ADAPTIVE ||
+      s->cfg.policy > GT_SERVE_SINGLE) {
     delete s;
     set_error("gt_serve_create: configuration out of range");
     return GT_EINVAL;
@@ -418,10 +528,13 @@ GT_API int gt_serve_destroy(gt_server_t s) {
   }
   s->cv_sched.notify_all();
   if (s->worker.joinable()) s->worker.join();
-  for (auto st : s->streams) {
-    cudaStreamSynchronize(st);
-    cudaStreamDestroy(st);
-  }
+  for (auto st : s->streams) cudaStreamSynchronize(st);
+  // single-root flights left the graphs pointing at the server's streams: all their work
+  // is done, so the graphs forget those streams before they are destroyed
+  for (auto& ge : s->graphs)
+    if (std::find(s->streams.begin(), s->streams.end(), ge.g->last_stream) != s->streams.end())
+      ge.g->last_stream = nullptr;
+  for (auto st : s->streams) cudaStreamDestroy(st);
   for (auto& c : s->ctxs) batch_ctx_free(&c);
   for (auto& ge : s->graphs)
     for (auto& b : ge.slots)

@@ -40,12 +40,15 @@ def test_struct_layouts_match_header(tmp_path):
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "gt.h"\n'
                     'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(gt_config), sizeof(gt_tuning),'
                     ' sizeof(gt_stats), sizeof(gt_level_info), offsetof(gt_stats, mh), offsetof(gt_level_info, frontier));'
+                    ' printf("%zu %zu %zu\\n", sizeof(gt_serve_config), offsetof(gt_serve_config, policy),'
+                    ' sizeof(gt_serve_stats));'
                     ' return 0;}\n')
     exe = tmp_path / "sizes"
     subprocess.check_call(["gcc", "-std=c11", "-I", INCLUDE, str(prog), "-o", str(exe)])
     got = list(map(int, subprocess.check_output([str(exe)]).split()))
     want = [ctypes.sizeof(gt.gt_config), ctypes.sizeof(gt.gt_tuning), ctypes.sizeof(gt.gt_stats),
-            ctypes.sizeof(gt.gt_level_info), gt.gt_stats.mh.offset, gt.gt_level_info.frontier.offset]
+            ctypes.sizeof(gt.gt_level_info), gt.gt_stats.mh.offset, gt.gt_level_info.frontier.offset,
+            ctypes.sizeof(gt.gt_serve_config), gt.gt_serve_config.policy.offset, ctypes.sizeof(gt.gt_serve_stats)]
     assert got == want
 
 
@@ -60,6 +63,12 @@ def test_defaults_and_errors_without_gpu():
     assert L.gt_graph_build(None, 0, 0, None, None, ctypes.byref(h)) == gt.GT_EINVAL
     assert L.gt_bfs(None, 0, None, None, None) == gt.GT_EINVAL
     assert b"n <= 2^31" in L.gt_last_error() or L.gt_last_error()
+    # server configuration is checked before the server touches a device
+    c = gt.gt_serve_config()
+    L.gt_serve_config_default(ctypes.byref(c))
+    assert (c.streams, c.max_batch_roots, c.policy) == (2, 256, gt.GT_SERVE_ADAPTIVE)
+    c.policy = 3
+    assert L.gt_serve_create(ctypes.byref(c), ctypes.byref(h)) == gt.GT_EINVAL
 
 
 def test_no_cpu_fallback_in_binding():
