@@ -68,7 +68,7 @@ typedef struct gt_tuning {
   int32_t td_grid_min;  /* top-down: degree above which the vertex's edges join one flat
                            edge space shared by the whole grid (2048) */
   int32_t bu_thread_scan; /* bottom-up: neighbours a lane checks alone before the warp
-                             takes the vertex over (8) */
+                             takes the vertex over (24) */
   int32_t blocks_per_sm;  /* CTAs per SM of the traversal kernels (8) */
   int32_t force_direction; /* 0 = switch heuristic, 1 = top-down only, 2 = bottom-up only */
   int32_t launch_mode;  /* 0 = whole level loop in one CUDA graph with device-side

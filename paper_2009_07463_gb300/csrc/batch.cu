@@ -54,6 +54,8 @@ struct SlotDev {
   const int32_t* ccol;
   const int32_t* vinfo;
   const int32_t* new2old;
+  const int32_t* anchor_cid;  // anchor -> core id (tree vertices name their anchor in vinfo)
+  const int32_t* anchor_vid;  // anchor -> vertex id
   const int32_t* up;
   const int32_t* old2core;
   // state (core ids)
@@ -395,9 +397,9 @@ __global__ void __launch_bounds__(BT) batch_output(SlotDev* slots, int nslots) {
       if (info >= 0) {
         cid = info;
       } else if (info <= -2 && info != INT32_MIN) {
-        cid = -2 - info;
+        cid = s.anchor_cid[-2 - info];
         add = 1;
-        fixed_parent = s.new2old[cid];
+        fixed_parent = s.anchor_vid[-2 - info];
       }
       const uint64_t vis = cid >= 0 ? s.visit[cid] : 0ull;
       for (int k = 0; k < 8; ++k) {
@@ -591,6 +593,8 @@ int batch_launch(BatchCtx* ctx, const SlotSpec* specs, int nspecs, int sm_share,
     d.ccol = g->core.col;
     d.vinfo = g->vinfo;
     d.new2old = g->new2old;
+    d.anchor_cid = g->anchor_cid;
+    d.anchor_vid = g->anchor_vid;
     d.up = g->up;
     d.old2core = g->old2core;
     d.visit = (uint64_t*)sp.mem[0];

@@ -35,6 +35,7 @@ struct BfsArgs {
   uint32_t* vis1;
   int32_t* queues;  // [2][NBINS][n]
   int32_t* ulist;
+  const int4* pre;         // adjacency prefix records (null: none)
   const int32_t* new2old;  // view id -> vertex id (null: the view's ids are vertex ids)
   BfsCtl* ctl;
   int32_t td_warp_min;
@@ -56,6 +57,7 @@ BfsArgs make_args(const View& v, const gt_tuning& t) {
   a.vis1 = v.vis[1];
   a.queues = v.queues;
   a.ulist = v.ulist;
+  a.pre = v.pre;
   a.new2old = v.new2old;
   a.ctl = v.ctl;
   a.td_warp_min = std::max(1, t.td_warp_min);
@@ -453,6 +455,7 @@ __global__ void __launch_bounds__(BFS_THREADS) bfs_bu_gather(BfsArgs a) {
 }
 
 constexpr int BU_V = 4;  // listed vertices a lane keeps in flight
+constexpr int CW = 2;    // 32-neighbour windows a warp keeps in flight on one long list
 
 __device__ __forceinline__ bool visited_bit(const uint32_t* __restrict__ vc, int32_t u) {
   return (__ldg(&vc[u >> 5]) >> (u & 31)) & 1u;
@@ -482,15 +485,21 @@ __device__ __forceinline__ bool in_frontier(const uint32_t* __restrict__ vc, con
   return visited_bit(vc, u);
 }
 
-// Scan: a warp takes 32 x BU_V consecutive listed vertices; each lane issues the row and
-// first-neighbour loads of its BU_V vertices together, then checks up to bu_thread_scan
-// neighbours per vertex alone, in ascending order, stopping at the first visited one.
-// Vertices still open are taken over by the whole warp, 32 neighbours per step, first hit
-// by ballot. A found vertex records (L+1, parent) and sets its bit in the next bitmap
-// (one atomic per distinct word); counts are committed once per CTA. The frontier
-// queue is not written here: the next bottom-up step reads the bitmap, and a top-down
-// step rebuilds the queue from the bitmaps first.
-template <bool HASH>
+// Scan: a warp takes 32 x BU_V consecutive listed vertices. With prefix records (PRE),
+// each lane reads the records of its BU_V vertices (degree and first three neighbours,
+// 16 bytes each, in list order) and tests all listed neighbours at once; only a vertex
+// with no hit among them and a larger degree goes on into the CSR, from its fourth
+// neighbour. Without records, each lane reads the row offsets and first neighbours of its
+// vertices together. Either way a lane then checks up to bu_thread_scan neighbours per
+// vertex alone (three of them from the record), depth by depth across its vertices, in
+// ascending order, stopping at the first visited one (visited before this level = in
+// the frontier, for an unvisited vertex). Vertices still open are taken over by the
+// whole warp, one at a time, 32 neighbours per step, first hit by ballot. A found vertex
+// records (L+1, parent) and sets its bit in the next bitmap (one atomic per distinct
+// word); counts are committed once per CTA. The frontier queue is not written here: the
+// next bottom-up step reads the bitmap, and a top-down step rebuilds the queue from the
+// bitmaps first.
+template <bool HASH, bool PRE>
 __global__ void __launch_bounds__(BFS_THREADS, 4) bfs_bu_scan(BfsArgs a) {
   extern __shared__ int32_t s_hash[];
   BfsCtl* ctl = a.ctl;
@@ -515,40 +524,80 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) bfs_bu_scan(BfsArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = gtid() >> 5, nw = gthreads() >> 5;
   const int64_t span = 32 * BU_V;
+  const int alone = PRE ? max(a.bu_scan - 3, 0) : max(a.bu_scan, 1);  // CSR probes per lane and vertex
   int64_t nf = 0, mf = 0, examined = 0;
   for (int64_t base = gw * span; base < nu; base += nw * span) {
-    int32_t w[BU_V], par[BU_V];
-    int64_t s[BU_V], e[BU_V], lim[BU_V];
+    int32_t w[BU_V], par[BU_V], d[BU_V];
+    int64_t s[BU_V], e[BU_V];
 #pragma unroll
     for (int j = 0; j < BU_V; ++j) {
       const int64_t i = base + j * 32 + lane;
       w[j] = i < nu ? a.ulist[i] : -1;
     }
+    if (PRE) {
+      int4 r[BU_V];
 #pragma unroll
-    for (int j = 0; j < BU_V; ++j) {
-      s[j] = 0;
-      e[j] = 0;
-      if (w[j] >= 0) {
-        s[j] = a.row[w[j]];
-        e[j] = a.row[w[j] + 1];
+      for (int j = 0; j < BU_V; ++j) r[j] = w[j] >= 0 ? __ldg(&a.pre[w[j]]) : make_int4(0, -1, -1, -1);
+      bool h0[BU_V], h1[BU_V], h2[BU_V];
+      if (HASH) {
+#pragma unroll
+        for (int j = 0; j < BU_V; ++j) {
+          h0[j] = r[j].y >= 0 && hash_has(s_hash, r[j].y);
+          h1[j] = !h0[j] && r[j].z >= 0 && hash_has(s_hash, r[j].z);
+          h2[j] = !h0[j] && !h1[j] && r[j].w >= 0 && hash_has(s_hash, r[j].w);
+        }
+      } else {
+        uint32_t b0[BU_V], b1[BU_V], b2[BU_V];
+#pragma unroll
+        for (int j = 0; j < BU_V; ++j) {
+          b0[j] = r[j].y >= 0 ? __ldg(&vc[r[j].y >> 5]) : 0u;
+          b1[j] = r[j].z >= 0 ? __ldg(&vc[r[j].z >> 5]) : 0u;
+          b2[j] = r[j].w >= 0 ? __ldg(&vc[r[j].w >> 5]) : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < BU_V; ++j) {
+          h0[j] = r[j].y >= 0 && ((b0[j] >> (r[j].y & 31)) & 1u);
+          h1[j] = r[j].z >= 0 && ((b1[j] >> (r[j].z & 31)) & 1u);
+          h2[j] = r[j].w >= 0 && ((b2[j] >> (r[j].w & 31)) & 1u);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < BU_V; ++j) {
+        par[j] = h0[j] ? r[j].y : h1[j] ? r[j].z : h2[j] ? r[j].w : -1;
+        d[j] = r[j].x;
+        examined += h0[j] ? 1 : h1[j] ? 2 : h2[j] ? 3 : min(r[j].x, 3);
+        s[j] = 0;
+        e[j] = 0;
+        if (w[j] >= 0 && par[j] < 0 && d[j] > 3) {
+          s[j] = a.row[w[j]] + 3;
+          e[j] = s[j] - 3 + d[j];
+        }
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < BU_V; ++j) {
+        par[j] = -1;
+        s[j] = 0;
+        e[j] = 0;
+        if (w[j] >= 0) {
+          s[j] = a.row[w[j]];
+          e[j] = a.row[w[j] + 1];
+        }
+        d[j] = (int32_t)(e[j] - s[j]);
       }
     }
     // probe depth by depth: at every depth the open vertices of this lane issue their
     // loads together, so BU_V dependent chains overlap
     int64_t nx[BU_V];
 #pragma unroll
-    for (int j = 0; j < BU_V; ++j) {
-      par[j] = -1;
-      nx[j] = s[j];
-      lim[j] = min(e[j], s[j] + (int64_t)max(a.bu_scan, 1));
-    }
-    for (int r = 0; r < max(a.bu_scan, 1); ++r) {
+    for (int j = 0; j < BU_V; ++j) nx[j] = s[j];
+    for (int rd = 0; rd < alone; ++rd) {
       int32_t u[BU_V];
       bool any = false;
 #pragma unroll
       for (int j = 0; j < BU_V; ++j) {
         u[j] = -1;
-        if (par[j] < 0 && nx[j] < lim[j]) {
+        if (par[j] < 0 && nx[j] < e[j] && nx[j] - s[j] < alone) {
           u[j] = a.col[nx[j]];
           any = true;
         }
@@ -583,33 +632,40 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) bfs_bu_scan(BfsArgs a) {
       if (fnd) {
         a.state[w[j]] = hi | orig_of(a, par[j]);
         ++nf;
-        mf += e[j] - s[j];
+        mf += d[j];
       }
       const unsigned peers = __match_any_sync(FULL, fnd ? (w[j] >> 5) : -1);
       const unsigned bits = __reduce_or_sync(peers, fnd ? (1u << (w[j] & 31)) : 0u);
       if (fnd && lane == __ffs(peers) - 1) atomicOr(&vn[w[j] >> 5], bits);
-      unsigned lm = __ballot_sync(FULL, w[j] >= 0 && !fnd && lim[j] < e[j]);
+      const int64_t lim = min(e[j], s[j] + (int64_t)alone);  // where this lane's own probes stopped
+      unsigned lm = __ballot_sync(FULL, w[j] >= 0 && !fnd && lim < e[j]);
       while (lm) {
         const int src = __ffs(lm) - 1;
         lm &= lm - 1;
         const int32_t w2 = __shfl_sync(FULL, w[j], src);
-        const int64_t s2 = __shfl_sync(FULL, lim[j], src), e2 = __shfl_sync(FULL, e[j], src);
-        const int64_t d2 = e2 - __shfl_sync(FULL, s[j], src);
+        const int64_t s2 = __shfl_sync(FULL, lim, src), e2 = __shfl_sync(FULL, e[j], src);
+        const int32_t d2 = __shfl_sync(FULL, d[j], src);
         int32_t par2 = -1;
-        for (int64_t b0 = s2; b0 < e2; b0 += 32) {
-          const int64_t k2 = b0 + lane;
-          int32_t u = 0;
-          bool hit = false;
-          if (k2 < e2) {
-            u = a.col[k2];
-            hit = in_frontier<HASH>(vc, s_hash, u);
+        for (int64_t b0 = s2; b0 < e2 && par2 < 0; b0 += 32 * CW) {
+          // CW windows of 32 neighbours in flight per lane, resolved in order
+          int32_t uu[CW];
+          bool hh[CW];
+#pragma unroll
+          for (int t = 0; t < CW; ++t) {
+            const int64_t k2 = b0 + 32 * t + lane;
+            uu[t] = k2 < e2 ? a.col[k2] : -1;
           }
-          const unsigned hm = __ballot_sync(FULL, hit);
-          if (lane == 0) examined += hm ? __ffs(hm) : min((int64_t)32, e2 - b0);
-          if (hm) {
-            par2 = __shfl_sync(FULL, u, __ffs(hm) - 1);
-            break;
+#pragma unroll
+          for (int t = 0; t < CW; ++t) hh[t] = uu[t] >= 0 && in_frontier<HASH>(vc, s_hash, uu[t]);
+#pragma unroll
+          for (int t = 0; t < CW; ++t) {
+            const unsigned hm = __ballot_sync(FULL, hh[t]);
+            if (par2 < 0 && hm) {
+              par2 = __shfl_sync(FULL, uu[t], __ffs(hm) - 1);
+              if (lane == 0) examined += 32 * t + __ffs(hm);
+            }
           }
+          if (par2 < 0 && lane == 0) examined += min((int64_t)(32 * CW), e2 - b0);
         }
         if (par2 >= 0 && lane == 0) {
           a.state[w2] = hi | orig_of(a, par2);
@@ -764,6 +820,10 @@ struct EtArgs {
   const int32_t* old2core;
   const int32_t* new2old;
   int64_t n;
+  const int32_t* anchor_cid;
+  const int32_t* anchor_vid;
+  uint64_t* anchor_out;
+  int64_t n_anchor;
 };
 
 // Alg. 9, root in an edge tree: follow up[] from the root to the first core vertex c
@@ -790,21 +850,28 @@ __global__ void et_start(BfsArgs a, EtArgs e, int32_t root, int32_t alpha, int32
   ctl_begin(a, start, hops, alpha, beta, force);
 }
 
+// What the tree children of each anchor (a core vertex that edge-tree vertices hang
+// from) inherit: level + 1 and the anchor's vertex id, packed like the state. The
+// anchors are a small set spread over the core; gathering them into one dense array
+// first lets the output pass read it from L2 instead of hitting the core state at
+// random once per tree vertex.
+__global__ void et_anchors(EtArgs e, const uint64_t* __restrict__ state) {
+  for (int64_t k = gtid(); k < e.n_anchor; k += gthreads()) {
+    const uint64_t st = state[e.anchor_cid[k]];
+    e.anchor_out[k] = st == UNVISITED ? UNVISITED : (((st >> 32) + 1) << 32) | (uint32_t)e.anchor_vid[k];
+  }
+}
+
 // Levels and parents of every vertex in vertex-id order: core vertices from the core
 // BFS state (parents already vertex ids), edge-tree vertices hanging from a core vertex
-// from that vertex's level (Alg. 7 / Alg. 10 with levels), tree vertices hanging from a
+// from their anchor's entry (Alg. 7 / Alg. 10 with levels), tree vertices hanging from a
 // tree vertex -2 ("resolve pending", see et_resolve), everything else -1.
-// Four consecutive vertices per thread: one 128-bit vinfo load, four independent state
-// gathers, four independent id gathers, 128-bit stores (when n and the outputs allow).
-__device__ __forceinline__ void et_decode(int32_t info, int32_t& cid, int32_t& add) {
-  cid = -1;
-  add = 0;
-  if (info >= 0) {
-    cid = info;
-  } else if (info != INT32_MIN && info <= -2) {
-    cid = -2 - info;
-    add = 1;
-  }
+// Four consecutive vertices per thread: one 128-bit vinfo load, four independent
+// gathers, 128-bit stores (when n and the outputs allow).
+__device__ __forceinline__ uint64_t et_packed(const EtArgs& e, const uint64_t* __restrict__ state, int32_t info) {
+  if (info >= 0) return state[info];
+  if (info != INT32_MIN && info <= -2) return e.anchor_out[-2 - info];
+  return UNVISITED;
 }
 
 __global__ void et_output(EtArgs e, const uint64_t* __restrict__ state, int32_t* __restrict__ parent,
@@ -813,39 +880,26 @@ __global__ void et_output(EtArgs e, const uint64_t* __restrict__ state, int32_t*
   for (int64_t i = gtid(); i < n4; i += gthreads()) {
     const int4 in = reinterpret_cast<const int4*>(e.vinfo)[i];
     const int32_t info[4] = {in.x, in.y, in.z, in.w};
-    int32_t cid[4], add[4], l[4], p[4];
     uint64_t st[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      et_decode(info[k], cid[k], add[k]);
-      st[k] = cid[k] >= 0 ? state[cid[k]] : UNVISITED;
-    }
+    for (int k = 0; k < 4; ++k) st[k] = et_packed(e, state, info[k]);
+    int32_t l[4], p[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      l[k] = info[k] == INT32_MIN ? -2 : -1;
-      p[k] = l[k];
-      if (st[k] != UNVISITED) {
-        l[k] = (int32_t)(st[k] >> 32) + add[k];
-        p[k] = add[k] ? e.new2old[cid[k]] : (int32_t)(uint32_t)st[k];
-      }
+      const bool r = st[k] != UNVISITED;
+      l[k] = r ? (int32_t)(st[k] >> 32) : (info[k] == INT32_MIN ? -2 : -1);
+      p[k] = r ? (int32_t)(uint32_t)st[k] : l[k];
     }
     reinterpret_cast<int4*>(level)[i] = make_int4(l[0], l[1], l[2], l[3]);
     reinterpret_cast<int4*>(parent)[i] = make_int4(p[0], p[1], p[2], p[3]);
   }
   for (int64_t v = 4 * n4 + gtid(); v < e.n; v += gthreads()) {
     const int32_t info = e.vinfo[v];
-    int32_t cid, add;
-    et_decode(info, cid, add);
-    int32_t l = info == INT32_MIN ? -2 : -1, p = l;
-    if (cid >= 0) {
-      const uint64_t st = state[cid];
-      if (st != UNVISITED) {
-        l = (int32_t)(st >> 32) + add;
-        p = add ? e.new2old[cid] : (int32_t)(uint32_t)st;
-      }
-    }
+    const uint64_t st = et_packed(e, state, info);
+    const bool r = st != UNVISITED;
+    const int32_t l = r ? (int32_t)(st >> 32) : (info == INT32_MIN ? -2 : -1);
     level[v] = l;
-    parent[v] = p;
+    parent[v] = r ? (int32_t)(uint32_t)st : l;
   }
 }
 
@@ -907,9 +961,14 @@ constexpr size_t HASH_SMEM = sizeof(int32_t) * HASH_SLOTS;
 
 // Lets the shared-memory-set variant of the scan take its 64 KB of dynamic shared memory.
 int prepare_kernels() {
-  return cuda_fail(cudaFuncSetAttribute(bfs_bu_scan<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  int rc = cuda_fail(cudaFuncSetAttribute(bfs_bu_scan<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)HASH_SMEM),
+                     "scan shared memory");
+  if (rc == GT_OK)
+    rc = cuda_fail(cudaFuncSetAttribute(bfs_bu_scan<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)HASH_SMEM),
                    "scan shared memory");
+  return rc;
 }
 
 // The step kernels of one level: 0 top-down, 1 bottom-up (gather + scan), 2 mark +
@@ -923,10 +982,17 @@ void launch_step(int kind, const BfsArgs& a, int grid, cudaStream_t s) {
   }
   if (kind == 2 || kind == 4) bfs_mark<<<grid, BFS_THREADS, 0, s>>>(a);
   bfs_bu_gather<<<grid, BFS_THREADS, 0, s>>>(a);
-  if (kind == 4)
-    bfs_bu_scan<true><<<grid, BFS_THREADS, HASH_SMEM, s>>>(a);
-  else
-    bfs_bu_scan<false><<<grid, BFS_THREADS, 0, s>>>(a);
+  if (kind == 4) {
+    if (a.pre)
+      bfs_bu_scan<true, true><<<grid, BFS_THREADS, HASH_SMEM, s>>>(a);
+    else
+      bfs_bu_scan<true, false><<<grid, BFS_THREADS, HASH_SMEM, s>>>(a);
+  } else {
+    if (a.pre)
+      bfs_bu_scan<false, true><<<grid, BFS_THREADS, 0, s>>>(a);
+    else
+      bfs_bu_scan<false, false><<<grid, BFS_THREADS, 0, s>>>(a);
+  }
 }
 
 unsigned host_step_kind(int dir, int need_mark, int need_queue, int bu_hash) {
@@ -1080,7 +1146,7 @@ int run_bfs(gt_graph* g, View& v, bool et, int64_t root, int32_t* parent, int32_
   if (timed) cudaEventRecord(g->phase_events[0], s);
   const int gs = grid_stream(g, std::max<int64_t>(v.n, v.nwords));
   bfs_reset<<<gs, 256, 0, s>>>(v.state, v.vis[0], v.n, v.nwords);
-  EtArgs e{g->vinfo, g->up, g->old2core, g->new2old, g->n};
+  EtArgs e{g->vinfo, g->up, g->old2core, g->new2old, g->n, g->anchor_cid, g->anchor_vid, g->anchor_out, g->n_anchor};
   if (et)
     et_start<<<1, 1, 0, s>>>(a, e, (int32_t)root, t.alpha, t.beta, t.force_direction);
   else
@@ -1094,6 +1160,7 @@ int run_bfs(gt_graph* g, View& v, bool et, int64_t root, int32_t* parent, int32_
   if (et) {
     const int go = grid_stream(g, g->n);
     const int vec = ((uintptr_t)parent % 16 == 0) && ((uintptr_t)level % 16 == 0);
+    if (g->n_anchor > 0) et_anchors<<<grid_stream(g, g->n_anchor), 256, 0, s>>>(e, v.state);
     et_output<<<go, 256, 0, s>>>(e, v.state, parent, level, vec);
     et_fixup<<<1, 1, 0, s>>>(e, (int32_t)root, parent, level);
     for (int h = 0; h < g->resolve_heights; ++h) {

@@ -248,12 +248,36 @@ __global__ void core_fill(const int64_t* __restrict__ row, const int32_t* __rest
 
 // ---- a4: edge-tree layout -----------------------------------------------------------
 
-// vinfo: core id for core vertices; -2 - (core id of up) for tree vertices hanging from
-// a core vertex; INT32_MIN for tree vertices hanging from another tree vertex (resolved
-// height by height, listed through rflag); -1 for the rest (zero-degree vertices, tops).
+// Anchors: core vertices that some edge-tree vertex hangs from (up[] is a core vertex).
+__global__ void mark_anchors(int64_t n, const uint8_t* __restrict__ vtype, const int32_t* __restrict__ up,
+                             const int32_t* __restrict__ old2core, uint8_t* __restrict__ aflag) {
+  for (int64_t v = gtid(); v < n; v += gthreads()) {
+    const uint8_t t = vtype[v];
+    if (t != GT_TREE_LEAF && t != GT_TREE_INTERNAL) continue;
+    const int32_t u = up[v];
+    if (u < 0) continue;
+    const int32_t cu = old2core[u];
+    if (cu >= 0) aflag[cu] = 1;
+  }
+}
+
+__global__ void list_anchors(int64_t nc, const uint8_t* __restrict__ aflag, const int32_t* __restrict__ apos,
+                             const int32_t* __restrict__ new2old, int32_t* __restrict__ anchor_cid,
+                             int32_t* __restrict__ anchor_vid) {
+  for (int64_t c = gtid(); c < nc; c += gthreads()) {
+    if (!aflag[c]) continue;
+    anchor_cid[apos[c]] = (int32_t)c;
+    anchor_vid[apos[c]] = new2old[c];
+  }
+}
+
+// vinfo: core id for core vertices; -2 - (anchor index of up) for tree vertices hanging
+// from a core vertex; INT32_MIN for tree vertices hanging from another tree vertex
+// (resolved height by height, listed through rflag); -1 for the rest (zero-degree
+// vertices, tops).
 __global__ void tree_info(int64_t n, const uint8_t* __restrict__ vtype, const int32_t* __restrict__ up,
-                          const int32_t* __restrict__ old2core, int32_t* __restrict__ vinfo,
-                          uint8_t* __restrict__ rflag) {
+                          const int32_t* __restrict__ old2core, const int32_t* __restrict__ apos,
+                          int32_t* __restrict__ vinfo, uint8_t* __restrict__ rflag) {
   for (int64_t v = gtid(); v < n; v += gthreads()) {
     const uint8_t t = vtype[v];
     int32_t info = -1;
@@ -265,7 +289,7 @@ __global__ void tree_info(int64_t n, const uint8_t* __restrict__ vtype, const in
       if (u >= 0) {
         const int32_t cu = old2core[u];
         if (cu >= 0) {
-          info = -2 - cu;
+          info = -2 - apos[cu];
         } else {
           info = INT32_MIN;
           f = 1;
@@ -337,8 +361,17 @@ int device_malloc(gt_graph* g, void** p, size_t bytes) {
   return GT_OK;
 }
 
+// Adjacency prefix records of a view: {degree, col[row[v]], col[row[v] + 1], col[row[v] + 2]},
+// -1 where the degree ends first.
+static __global__ void build_prefix(const int64_t* __restrict__ row, const int32_t* __restrict__ col, int64_t n,
+                             int4* __restrict__ pre) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = row[v], d = row[v + 1] - b;
+    pre[v] = make_int4((int32_t)d, d > 0 ? col[b] : -1, d > 1 ? col[b + 1] : -1, d > 2 ? col[b + 2] : -1);
+  }
+}
+
 int alloc_view_state(gt_graph* g, View& v, cudaStream_t s) {
-  (void)s;
   const int64_t n = v.n > 0 ? v.n : 1;
   v.nwords = (n + 31) / 32;
   v.nwords = (v.nwords + BU_CHUNK_WORDS - 1) / BU_CHUNK_WORDS * BU_CHUNK_WORDS;
@@ -349,7 +382,9 @@ int alloc_view_state(gt_graph* g, View& v, cudaStream_t s) {
   if ((rc = device_malloc(g, (void**)&v.queues, sizeof(int32_t) * n * 2 * NBINS))) return rc;
   if ((rc = device_malloc(g, (void**)&v.ulist, sizeof(int32_t) * n))) return rc;
   if ((rc = device_malloc(g, (void**)&v.ctl, sizeof(BfsCtl)))) return rc;
-  return GT_OK;
+  if ((rc = device_malloc(g, (void**)&v.pre, sizeof(int4) * n))) return rc;
+  if (v.n > 0) build_prefix<<<grid_for(g, v.n), BT, 0, s>>>(v.row, v.col, v.n, v.pre);
+  return cuda_fail(cudaGetLastError(), "prefix records");
 }
 
 static void free_view(View& v) {
@@ -358,6 +393,7 @@ static void free_view(View& v) {
   cudaFree(v.queues);
   cudaFree(v.ulist);
   cudaFree(v.ctl);
+  cudaFree(v.pre);
   v = View{};
 }
 
@@ -380,6 +416,9 @@ void free_graph(gt_graph* g) {
   cudaFree(g->vtype);
   cudaFree(g->up);
   cudaFree(g->vinfo);
+  cudaFree(g->anchor_cid);
+  cudaFree(g->anchor_vid);
+  cudaFree(g->anchor_out);
   cudaFree(g->new2old);
   cudaFree(g->old2core);
   free_batch_mem(g);
@@ -569,10 +608,25 @@ int build_graph(gt_graph* g, const int64_t* edges, int64_t m, int64_t n, cudaStr
   if (nc > 0) core_fill<<<gw, BT, 0, s>>>(g->row, g->col, is_core, g->new2old, g->old2core, nc, cv.row, cv.col);
   TRYC(cudaGetLastError(), "core csr");
 
-  // ---- a4: tree layout
+  // ---- a4: anchors and tree layout
+  uint8_t* aflag;
+  int32_t* apos;
+  TRY(tmp_malloc(tmp, (void**)&aflag, std::max<int64_t>(nc, 1)));
+  TRY(tmp_malloc(tmp, (void**)&apos, sizeof(int32_t) * (nc + 1)));
+  TRYC(cudaMemsetAsync(aflag, 0, std::max<int64_t>(nc, 1), s), "memset");
+  mark_anchors<<<gn, BT, 0, s>>>(n, g->vtype, g->up, g->old2core, aflag);
+  TRY(scan_u8_to_i32(aflag, apos, nc, s, d_scan, scan_bytes));
+  int32_t na32 = 0;
+  TRYC(cudaMemcpyAsync(&na32, apos + nc, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "readback");
+  TRYC(cudaStreamSynchronize(s), "sync");
+  g->n_anchor = na32;
+  TRY(device_malloc(g, (void**)&g->anchor_cid, sizeof(int32_t) * std::max<int64_t>(na32, 1)));
+  TRY(device_malloc(g, (void**)&g->anchor_vid, sizeof(int32_t) * std::max<int64_t>(na32, 1)));
+  TRY(device_malloc(g, (void**)&g->anchor_out, sizeof(uint64_t) * std::max<int64_t>(na32, 1)));
+  if (nc > 0) list_anchors<<<grid_for(g, nc), BT, 0, s>>>(nc, aflag, apos, g->new2old, g->anchor_cid, g->anchor_vid);
   TRY(device_malloc(g, (void**)&g->vinfo, sizeof(int32_t) * n));
   uint8_t* rflag = is_core;  // is_core is consumed; reuse its storage
-  tree_info<<<gn, BT, 0, s>>>(n, g->vtype, g->up, g->old2core, g->vinfo, rflag);
+  tree_info<<<gn, BT, 0, s>>>(n, g->vtype, g->up, g->old2core, apos, g->vinfo, rflag);
   TRY(scan_u8_to_i32(rflag, pos, n, s, d_scan, scan_bytes));
   int32_t nres = 0;
   TRYC(cudaMemcpyAsync(&nres, pos + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "readback");

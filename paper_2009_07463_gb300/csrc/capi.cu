@@ -156,7 +156,7 @@ GT_API void gt_tuning_default(gt_tuning* t) {
   t->td_warp_min = 32;
   t->td_cta_min = 256;
   t->td_grid_min = 2048;
-  t->bu_thread_scan = 8;
+  t->bu_thread_scan = 24;
   t->blocks_per_sm = 8;
   t->force_direction = 0;
   t->launch_mode = 0;

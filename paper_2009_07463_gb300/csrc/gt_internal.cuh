@@ -63,6 +63,9 @@ struct View {
   uint32_t* vis[2] = {nullptr, nullptr};
   int32_t* queues = nullptr;   // 2 x NBINS queues of n entries: [set][bin][n]
   int32_t* ulist = nullptr;    // bottom-up: ascending list of unvisited vertices
+  // per vertex {degree, first three neighbours in ascending order (-1 past the degree)}:
+  // one sequential 16-byte read answers most bottom-up probes (null: probe the CSR only)
+  int4* pre = nullptr;
   const int32_t* new2old = nullptr;  // view id -> vertex id (core view); null when ids agree
   BfsCtl* ctl = nullptr;
 };
@@ -97,8 +100,13 @@ struct gt_graph {
   int32_t* deg = nullptr;       // cleaned degree per vertex
   uint8_t* vtype = nullptr;     // Alg. 8 classes
   int32_t* up = nullptr;        // edge-tree vertex -> the neighbour it hangs from (-1 top / none)
-  int32_t* vinfo = nullptr;     // >= 0 core id; -2 - x: tree vertex hanging from core id x;
+  int32_t* vinfo = nullptr;     // >= 0 core id; -2 - k: tree vertex hanging from anchor k;
                                 // INT32_MIN: tree vertex hanging from a tree vertex; -1 other
+  // anchors: the core vertices that edge-tree vertices hang from, in core-id order
+  int64_t n_anchor = 0;
+  int32_t* anchor_cid = nullptr;  // anchor -> core id
+  int32_t* anchor_vid = nullptr;  // anchor -> vertex id
+  uint64_t* anchor_out = nullptr; // per traversal: (level + 1) << 32 | vertex id, for its tree children
   int32_t* new2old = nullptr;   // core id -> vertex id
   int32_t* old2core = nullptr;  // vertex id -> core id or -1
   int32_t* resolve_list = nullptr;  // tree vertices whose up is a tree vertex, by height desc

@@ -106,7 +106,7 @@ int autotune(gt_graph* g, int nsample, uint64_t seed, cudaStream_t s, gt_tuning*
       {&gt_tuning::td_warp_min, {8, 16, 32, 64}, false},
       {&gt_tuning::td_cta_min, {128, 256, 512, 1024}, false},
       {&gt_tuning::td_grid_min, {1024, 2048, 4096, 16384}, false},
-      {&gt_tuning::bu_thread_scan, {2, 4, 8, 16, 32}, false},
+      {&gt_tuning::bu_thread_scan, {8, 16, 24, 32, 48}, false},
       {&gt_tuning::blocks_per_sm, {2, 4, 6, 8}, false},
       {&gt_tuning::batch_alpha, {2, 4, 8, 14, 32}, true},
       {&gt_tuning::batch_beta, {4, 12, 24, 64}, true},
