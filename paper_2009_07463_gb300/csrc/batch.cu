@@ -4,13 +4,17 @@
 // of the slot's roots, whether the vertex is visited (visit), in the current frontier
 // (front) or in the next one. Every adjacency read then serves all 64 roots. All slots
 // of all graphs advance level by level inside ONE persistent cooperative launch; grid
-// barriers separate the three phases of a level:
-//   E  expand   top-down slots push front bits along frontier edges (atomicOr) and list
-//               each newly reached vertex once; bottom-up slots pull: every vertex still
-//               missing some lanes scans its ascending adjacency, the first neighbour
-//               carrying a lane's frontier bit is that lane's parent (so min-id).
-//   P  commit   for vertices reached top-down, one ascending scan assigns each lane its
-//               smallest frontier neighbour; every reached lane gets its level; visit |=.
+// barriers separate the phases of a level:
+//   E  expand   top-down slots push front bits along frontier edges (atomicOr; the first
+//               to reach a vertex lists it) and take, per lane, the smallest frontier
+//               neighbour as parent (atomicMin); a long frontier adjacency is cut into
+//               chunks, the first pushed by the vertex's warp, the rest queued. Bottom-up
+//               slots pull: every vertex still missing some lanes scans its ascending
+//               adjacency, and the first neighbour carrying a lane's frontier bit is that
+//               lane's parent (so min-id); short adjacencies a lane each, long ones in
+//               chunks a warp each, chunk results merged by atomicMin.
+//   E2 queued   every warp takes queued top-down chunks (only when some slot queued any).
+//   P  commit   every reached lane gets its level; visit |= new lanes.
 //   D  decide   clear the old frontier words, swap, pick the next direction per slot.
 // Per lane the levels and parents equal those of a single-root gt_bfs (Alg. 9): each
 // lane is an ordinary BFS from its root's core vertex, levels are shared iterations, and
@@ -33,12 +37,8 @@ namespace gt {
 namespace {
 
 constexpr int BT = 256;
-constexpr int BW = BT / 32;
 constexpr int MAX_SLOTS_SMEM = 256;
-// Neighbours a lane scans alone (two dependent loads each) before its warp continues the
-// scan 32 entries per step; multi-source scans rarely stop early, so most of the work is
-// best done by the coalesced warp-wide path.
-constexpr int THREAD_SCAN = 4;
+constexpr int CW = 4;  // 32-entry windows a warp keeps in flight on one adjacency
 
 struct LaneInit {
   int32_t start;    // core id the lane's BFS starts from (-1: nothing to traverse)
@@ -58,12 +58,16 @@ struct SlotDev {
   const int32_t* anchor_vid;  // anchor -> vertex id
   const int32_t* up;
   const int32_t* old2core;
+  const int32_t* lanes;   // bottom-up work: short adjacencies, a lane each
+  const uint64_t* items;  // bottom-up work: (vertex << 32 | chunk) for long ones, a warp each
+  int64_t n_lanes, n_items;
   // state (core ids)
   uint64_t* visit;
   uint64_t* front[2];
   int32_t* P;   // [nc][64] parent vertex ids
   uint16_t* L;  // [nc][64] iteration at which the lane reached the vertex
   int32_t* fl[2];
+  uint64_t* q;  // top-down: (vertex << 32 | chunk) of long frontier adjacencies, second pass
   // outputs: lane l writes parent / level arrays outp[l] / outl[l] (n entries each)
   int32_t* outp[64];
   int32_t* outl[64];
@@ -77,6 +81,7 @@ struct SlotDev {
 struct SlotCtl {
   int64_t fl_n[2];
   int64_t m_next;  // summed degree of the next frontier
+  int64_t q_n;     // top-down chunk queue entries
   int32_t cur, dir, done, iter;
 };
 
@@ -86,8 +91,6 @@ struct BatchCtl {
   int live;          // slots not done
   int pad;
 };
-
-__device__ __forceinline__ int64_t deg(const SlotDev& s, int32_t v) { return s.crow[v + 1] - s.crow[v]; }
 
 // Grid-wide barrier for a cooperative launch: arrivals counted on one word, each CTA
 // waits for its generation's total. Bounded: after ~2^26 polls (seconds) it raises err.
@@ -120,73 +123,147 @@ __device__ bool grid_barrier(BatchCtl* bc, unsigned int& gen) {
   return s_ok;
 }
 
+// Sets level `it` for the lanes in `lanes` of w's staged row: per group of 8 lanes (16 B)
+// one vector read-modify-write instead of one 2-byte store per lane.
 __device__ __forceinline__ void set_lane_levels(const SlotDev& s, int32_t w, uint64_t lanes, uint16_t it) {
-  uint16_t* row = s.L + (int64_t)w * 64;
-  while (lanes) {
-    const int l = __ffsll((long long)lanes) - 1;
-    lanes &= lanes - 1;
-    row[l] = it;
+  uint4* row = reinterpret_cast<uint4*>(s.L + (int64_t)w * 64);
+  const uint32_t it2 = (uint32_t)it * 0x10001u;
+  for (int q = 0; q < 8; ++q) {
+    const uint32_t m8 = (uint32_t)(lanes >> (8 * q)) & 0xFFu;
+    if (!m8) continue;
+    uint4 x = m8 == 0xFFu ? make_uint4(0, 0, 0, 0) : row[q];
+    uint32_t* xw = reinterpret_cast<uint32_t*>(&x);
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const uint32_t keep = ((m8 >> (2 * h)) & 1u ? 0u : 0xFFFFu) | ((m8 >> (2 * h + 1)) & 1u ? 0u : 0xFFFF0000u);
+      xw[h] = (xw[h] & keep) | (it2 & ~keep);
+    }
+    row[q] = x;
   }
 }
 
-// Ascending scan of w's adjacency assigning, for each lane of `want`, the first
-// neighbour whose frontier word carries that lane. One thread. Returns the lanes found.
-__device__ __forceinline__ uint64_t first_hits_thread(const SlotDev& s, const uint64_t* __restrict__ fc, int32_t w,
-                                                      uint64_t want, int64_t b, int64_t e, int64_t* stop) {
-  uint64_t got = 0;
+// Ascending scan of entries [b, e) of w's adjacency by one thread, assigning each lane of
+// `want` not yet in `got` the first neighbour whose frontier word carries it (so the
+// smallest). Four entries and their frontier words are loaded together per step.
+__device__ __forceinline__ uint64_t hits_thread(const SlotDev& s, const uint64_t* __restrict__ fc, int32_t w,
+                                                uint64_t want, uint64_t got, int64_t b, int64_t e) {
   int32_t* prow = s.P + (int64_t)w * 64;
-  int64_t k = b;
-  for (; k < e && got != want; ++k) {
-    const int32_t u = s.ccol[k];
-    uint64_t h = fc[u] & want & ~got;
-    if (h) {
-      got |= h;
-      const int32_t uo = s.new2old[u];
-      while (h) {
-        const int l = __ffsll((long long)h) - 1;
-        h &= h - 1;
-        prow[l] = uo;
+  for (int64_t k = b; k < e && got != want; k += 4) {
+    int32_t u[4];
+    uint64_t f[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) u[t] = k + t < e ? s.ccol[k + t] : -1;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) f[t] = u[t] >= 0 ? fc[u[t]] : 0ull;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      uint64_t h = f[t] & want & ~got;
+      if (h) {
+        got |= h;
+        const int32_t uo = s.new2old[u[t]];
+        while (h) {
+          const int l = __ffsll((long long)h) - 1;
+          h &= h - 1;
+          prow[l] = uo;
+        }
       }
     }
   }
-  *stop = k;
   return got;
 }
 
-// Warp-cooperative continuation of the same scan from entry b: 32 neighbours per step;
-// an exclusive OR-scan over lanes gives each neighbour the lanes it hits first.
-__device__ __forceinline__ uint64_t first_hits_warp(const SlotDev& s, const uint64_t* __restrict__ fc, int32_t w,
-                                                    uint64_t want, uint64_t got, int64_t b, int64_t e) {
+// The same scan by a whole warp over entries [b, e), CW windows of 32 entries in flight;
+// per window an inclusive OR-scan over the lanes gives each entry the lanes it supplies
+// first. ATOMIC: other warps scan other chunks of the same adjacency, so a parent is
+// taken with atomicMin (ascending entries = ascending ids: the smallest chunk wins).
+template <bool ATOMIC>
+__device__ __forceinline__ uint64_t hits_warp(const SlotDev& s, const uint64_t* __restrict__ fc, int32_t w,
+                                              uint64_t want, uint64_t got, int64_t b, int64_t e) {
   const int lane = threadIdx.x & 31;
   int32_t* prow = s.P + (int64_t)w * 64;
-  for (int64_t k0 = b; k0 < e && got != want; k0 += 32) {
-    const int64_t k = k0 + lane;
-    int32_t u = -1;
-    uint64_t h = 0;
-    if (k < e) {
-      u = s.ccol[k];
-      h = fc[u] & want & ~got;
-    }
-    uint64_t before = h;  // inclusive OR-scan, then exclude own
+  for (int64_t k0 = b; k0 < e && got != want; k0 += 32 * CW) {
+    int32_t u[CW];
+    uint64_t h[CW];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint64_t y = __shfl_up_sync(FULL, before, o);
-      if (lane >= o) before |= y;
+    for (int t = 0; t < CW; ++t) {
+      const int64_t k = k0 + 32 * t + lane;
+      u[t] = k < e ? s.ccol[k] : -1;
     }
-    const uint64_t excl = __shfl_up_sync(FULL, before, 1);
-    const uint64_t mine = h & ~(lane ? excl : 0ull);
-    if (mine) {
-      const int32_t uo = s.new2old[u];
-      uint64_t x = mine;
-      while (x) {
-        const int l = __ffsll((long long)x) - 1;
-        x &= x - 1;
-        prow[l] = uo;
+#pragma unroll
+    for (int t = 0; t < CW; ++t) h[t] = u[t] >= 0 ? fc[u[t]] & want : 0ull;
+#pragma unroll
+    for (int t = 0; t < CW; ++t) {
+      const uint64_t ht = h[t] & ~got;
+      if (!__any_sync(FULL, ht != 0)) continue;
+      uint64_t incl = ht;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl |= y;
       }
+      const uint64_t excl = __shfl_up_sync(FULL, incl, 1);
+      uint64_t mine = ht & ~(lane ? excl : 0ull);
+      if (mine) {
+        const int32_t uo = s.new2old[u[t]];
+        while (mine) {
+          const int l = __ffsll((long long)mine) - 1;
+          mine &= mine - 1;
+          if (ATOMIC)
+            atomicMin((unsigned int*)&prow[l], (unsigned int)uo);
+          else
+            prow[l] = uo;
+        }
+      }
+      got |= __shfl_sync(FULL, incl, 31);
     }
-    got |= __shfl_sync(FULL, before, 31);
   }
   return got;
+}
+
+// Appends the lanes with `first` set to a slot's next frontier list (one atomic per warp).
+__device__ __forceinline__ void list_append(bool first, int32_t w, int64_t* count, int32_t* list) {
+  const unsigned bal = __ballot_sync(FULL, first);
+  if (!bal) return;
+  const int lane = threadIdx.x & 31;
+  unsigned long long p = 0;
+  if (lane == __ffs(bal) - 1) p = atomicAdd((unsigned long long*)count, (unsigned long long)__popc(bal));
+  p = __shfl_sync(FULL, p, __ffs(bal) - 1);
+  if (first) list[p + __popc(bal & lanemask_lt())] = w;
+}
+
+// Top-down push along entries [b, e) of frontier vertex v (vertex id vo, frontier word
+// f), a warp, CW windows in flight: each neighbour gets the lanes it lacks ORed into its
+// next word (the first to give it any lists it) and, per lane, the smallest frontier
+// neighbour as parent by atomicMin.
+__device__ __forceinline__ void td_push(const SlotDev& s, uint64_t f, int32_t vo, int64_t b, int64_t e,
+                                        uint64_t* fn, int64_t* count, int32_t* list) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t k0 = b; k0 < e; k0 += 32 * CW) {
+    int32_t w[CW];
+    uint64_t vis[CW];
+#pragma unroll
+    for (int t = 0; t < CW; ++t) {
+      const int64_t k = k0 + 32 * t + lane;
+      w[t] = k < e ? s.ccol[k] : -1;
+    }
+#pragma unroll
+    for (int t = 0; t < CW; ++t) vis[t] = w[t] >= 0 ? s.visit[w[t]] : ~0ull;
+#pragma unroll
+    for (int t = 0; t < CW; ++t) {
+      uint64_t nb = f & ~vis[t];
+      bool first = false;
+      if (nb) {
+        first = atomicOr((unsigned long long*)&fn[w[t]], (unsigned long long)nb) == 0ull;
+        unsigned int* prow = (unsigned int*)(s.P + (int64_t)w[t] * 64);
+        while (nb) {
+          const int l = __ffsll((long long)nb) - 1;
+          nb &= nb - 1;
+          atomicMin(&prow[l], (unsigned int)vo);
+        }
+      }
+      list_append(first, w[t], count, list);
+    }
+  }
 }
 
 __global__ void batch_init(SlotDev* slots, SlotCtl* sctl, int nslots) {
@@ -236,109 +313,95 @@ __global__ void __launch_bounds__(BT) batch_run(SlotDev* slots, SlotCtl* sctl, i
       const uint64_t* fc = s.front[cur];
       uint64_t* fn = s.front[nxt];
       if (s_dir[si] == DIR_TD) {
+        // push: a warp per frontier vertex; of a long adjacency only the first chunk here,
+        // the others are queued for the second pass, where every warp takes chunks
         const int64_t nf = s_ncur[si];
-        for (int64_t j = gw; j < nf; j += nw) {  // a warp per frontier vertex
+        for (int64_t j = gw; j < nf; j += nw) {
           const int32_t v = s.fl[cur][j];
-          const uint64_t f = fc[v];
           const int64_t b = s.crow[v], e = s.crow[v + 1];
-          for (int64_t k0 = b; k0 < e; k0 += 32) {
-            const int64_t k = k0 + lane;
-            bool first = false;
-            int32_t w = 0;
-            if (k < e) {
-              w = s.ccol[k];
-              const uint64_t nb = f & ~s.visit[w];
-              if (nb) first = atomicOr((unsigned long long*)&fn[w], (unsigned long long)nb) == 0ull;
-            }
-            const unsigned bal = __ballot_sync(FULL, first);
-            if (bal) {
-              unsigned long long p = 0;
-              if (lane == __ffs(bal) - 1)
-                p = atomicAdd((unsigned long long*)&sctl[si].fl_n[nxt], (unsigned long long)__popc(bal));
-              p = __shfl_sync(FULL, p, __ffs(bal) - 1);
-              if (first) s.fl[nxt][p + __popc(bal & lanemask_lt())] = w;
-            }
+          const int64_t nch = (e - b + BATCH_CHUNK - 1) / BATCH_CHUNK;
+          if (nch > 1 && lane == 0) {
+            const unsigned long long p =
+                atomicAdd((unsigned long long*)&sctl[si].q_n, (unsigned long long)(nch - 1));
+            for (int64_t c = 1; c < nch; ++c) s.q[p + c - 1] = ((uint64_t)v << 32) | (uint32_t)c;
           }
+          td_push(s, fc[v], s.new2old[v], b, min(e, b + BATCH_CHUNK), fn, &sctl[si].fl_n[nxt], s.fl[nxt]);
         }
       } else {
+        // pull: every core vertex still missing lanes scans its ascending adjacency for the
+        // first neighbour carrying each missing lane (min-id parents). Short adjacencies:
+        // a lane each; long ones: chunks, a warp each, parents by atomicMin.
         const uint64_t act = s.active;
-        for (int64_t w0 = gw * 32; w0 < s.nc; w0 += nw * 32) {  // a lane per vertex, warp per 32
-          const int32_t w = (int32_t)(w0 + lane);
-          uint64_t miss = 0;
-          int64_t b = 0, e = 0, stop = 0;
+        for (int64_t i0 = gw * 32; i0 < s.n_lanes; i0 += nw * 32) {
+          const int64_t i = i0 + lane;
+          int32_t w = -1;
           uint64_t got = 0;
-          if (w < s.nc) {
-            miss = act & ~s.visit[w];
-            if (miss) {
-              b = s.crow[w];
-              e = s.crow[w + 1];
-              got = first_hits_thread(s, fc, w, miss, b, min(e, b + THREAD_SCAN), &stop);
+          if (i < s.n_lanes) {
+            w = s.lanes[i];
+            const uint64_t miss = act & ~s.visit[w];
+            if (miss) got = hits_thread(s, fc, w, miss, 0ull, s.crow[w], s.crow[w + 1]);
+          }
+          if (got) fn[w] = got;
+          list_append(got != 0, w, &sctl[si].fl_n[nxt], s.fl[nxt]);
+        }
+        for (int64_t it = gw; it < s.n_items; it += nw) {
+          const uint64_t item = s.items[it];
+          const int32_t w = (int32_t)(item >> 32);
+          const uint64_t miss = act & ~s.visit[w];
+          if (!miss) continue;
+          const int64_t rb = s.crow[w], re = s.crow[w + 1];
+          const int64_t b = rb + (int64_t)(uint32_t)item * BATCH_CHUNK, e = min(re, b + BATCH_CHUNK);
+          const bool whole = b == rb && e == re;
+          const uint64_t got = whole ? hits_warp<false>(s, fc, w, miss, 0ull, b, e)
+                                     : hits_warp<true>(s, fc, w, miss, 0ull, b, e);
+          bool first = false;
+          if (got && lane == 0) {
+            if (whole) {
+              fn[w] = got;
+              first = true;
+            } else {
+              first = atomicOr((unsigned long long*)&fn[w], (unsigned long long)got) == 0ull;
             }
           }
-          unsigned lm = __ballot_sync(FULL, miss && got != miss && stop < e);
-          while (lm) {  // long adjacency: the warp continues the scan
-            const int src = __ffs(lm) - 1;
-            lm &= lm - 1;
-            const int32_t w2 = __shfl_sync(FULL, w, src);
-            const uint64_t want2 = __shfl_sync(FULL, miss, src);
-            const uint64_t got2 = __shfl_sync(FULL, got, src);
-            const int64_t b2 = __shfl_sync(FULL, stop, src), e2 = __shfl_sync(FULL, e, src);
-            const uint64_t g2 = first_hits_warp(s, fc, w2, want2, got2, b2, e2);
-            if (lane == src) got = g2;
-          }
-          const bool first = got != 0;
-          if (first) fn[w] = got;
-          const unsigned bal = __ballot_sync(FULL, first);
-          if (bal) {
-            unsigned long long p = 0;
-            if (lane == __ffs(bal) - 1)
-              p = atomicAdd((unsigned long long*)&sctl[si].fl_n[nxt], (unsigned long long)__popc(bal));
-            p = __shfl_sync(FULL, p, __ffs(bal) - 1);
-            if (first) s.fl[nxt][p + __popc(bal & lanemask_lt())] = w;
-          }
+          list_append(first, w, &sctl[si].fl_n[nxt], s.fl[nxt]);
         }
       }
     }
     if (!grid_barrier(bc, gen)) return;
-    // ---- P: parents of top-down discoveries, levels, visit
+    // ---- E2: queued chunks of long top-down adjacencies (all slots, one pass)
+    bool any_q = false;
+    for (int si = 0; si < nslots; ++si) {
+      if (s_done[si] || s_dir[si] != DIR_TD) continue;
+      const int64_t nq = sctl[si].q_n;
+      if (nq == 0) continue;
+      any_q = true;
+      const SlotDev& s = slots[si];
+      const int cur = s_cur[si], nxt = cur ^ 1;
+      for (int64_t j = gw; j < nq; j += nw) {
+        const uint64_t item = s.q[j];
+        const int32_t v = (int32_t)(item >> 32);
+        const int64_t rb = s.crow[v], re = s.crow[v + 1];
+        const int64_t b = rb + (int64_t)(uint32_t)item * BATCH_CHUNK;
+        td_push(s, s.front[cur][v], s.new2old[v], b, min(re, b + BATCH_CHUNK), s.front[nxt], &sctl[si].fl_n[nxt],
+                s.fl[nxt]);
+      }
+    }
+    if (any_q && !grid_barrier(bc, gen)) return;
+    // ---- P: levels and visit of the discoveries
     for (int si = 0; si < nslots; ++si) {
       if (s_done[si]) continue;
       const SlotDev& s = slots[si];
       const int cur = s_cur[si], nxt = cur ^ 1;
-      const uint64_t* fc = s.front[cur];
       const uint64_t* fn = s.front[nxt];
       const int64_t nn = sctl[si].fl_n[nxt];
       const uint16_t it = (uint16_t)(s_it[si] + 1);
       int64_t msum = 0;
-      for (int64_t j0 = gw * 32; j0 < nn; j0 += nw * 32) {
-        const int64_t j = j0 + lane;
-        int32_t w = -1;
-        uint64_t nb = 0, got = 0;
-        int64_t b = 0, e = 0, stop = 0;
-        if (j < nn) {
-          w = s.fl[nxt][j];
-          nb = fn[w];
-          b = s.crow[w];
-          e = s.crow[w + 1];
-          msum += e - b;
-          if (s_dir[si] == DIR_TD) got = first_hits_thread(s, fc, w, nb, b, min(e, b + THREAD_SCAN), &stop);
-          else got = nb;
-        }
-        unsigned lm = __ballot_sync(FULL, w >= 0 && got != nb);
-        while (lm) {
-          const int src = __ffs(lm) - 1;
-          lm &= lm - 1;
-          const int32_t w2 = __shfl_sync(FULL, w, src);
-          const uint64_t want2 = __shfl_sync(FULL, nb, src);
-          const uint64_t got2 = __shfl_sync(FULL, got, src);
-          const int64_t b2 = __shfl_sync(FULL, stop, src), e2 = __shfl_sync(FULL, e, src);
-          const uint64_t g2 = first_hits_warp(s, fc, w2, want2, got2, b2, e2);
-          if (lane == src) got = g2;
-        }
-        if (w >= 0) {
-          set_lane_levels(s, w, nb, it);
-          s.visit[w] |= nb;
-        }
+      for (int64_t j = gtid(); j < nn; j += gthreads()) {
+        const int32_t w = s.fl[nxt][j];
+        const uint64_t nb = fn[w];
+        msum += s.crow[w + 1] - s.crow[w];
+        set_lane_levels(s, w, nb, it);
+        s.visit[w] |= nb;
       }
       msum = warp_sum(msum);
       if (lane == 0 && msum) atomicAdd((unsigned long long*)&sctl[si].m_next, (unsigned long long)msum);
@@ -360,6 +423,7 @@ __global__ void __launch_bounds__(BT) batch_run(SlotDev* slots, SlotCtl* sctl, i
         const int cur = s_cur[si], nxt = cur ^ 1;
         const int64_t nn = c.fl_n[nxt];
         c.fl_n[cur] = 0;
+        c.q_n = 0;
         c.cur = nxt;
         c.iter = s_it[si] + 1;
         if (nn == 0 || c.iter >= 65534) {
@@ -388,6 +452,17 @@ __global__ void __launch_bounds__(BT) batch_output(SlotDev* slots, int nslots) {
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   for (int si = 0; si < nslots; ++si) {
     const SlotDev& s = slots[si];
+    const int nl = min(8, s.nlanes - wp * 8);  // lanes of the slot this warp writes
+    if (nl <= 0) continue;
+    int32_t* op[8];
+    int32_t* ol[8];
+    int32_t base[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      op[k] = k < nl ? s.outp[wp * 8 + k] : nullptr;
+      ol[k] = k < nl ? s.outl[wp * 8 + k] : nullptr;
+      base[k] = k < nl ? s.lane[wp * 8 + k].base : 0;
+    }
     const int64_t nchunks = (s.n + 31) / 32;
     for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
       const int64_t v = c * 32 + lane;
@@ -401,19 +476,27 @@ __global__ void __launch_bounds__(BT) batch_output(SlotDev* slots, int nslots) {
         add = 1;
         fixed_parent = s.anchor_vid[-2 - info];
       }
-      const uint64_t vis = cid >= 0 ? s.visit[cid] : 0ull;
+      const uint32_t vis = cid >= 0 ? (uint32_t)(s.visit[cid] >> (wp * 8)) & 0xFFu : 0u;
+      // this warp's 8 lanes of the vertex's staged row: 16 B of levels, 32 B of parents
+      uint4 lv8 = make_uint4(0, 0, 0, 0);
+      int4 pa0 = make_int4(0, 0, 0, 0), pa1 = pa0;
+      if (vis) {
+        lv8 = *reinterpret_cast<const uint4*>(s.L + (int64_t)cid * 64 + wp * 8);
+        if (!add) {
+          pa0 = *reinterpret_cast<const int4*>(s.P + (int64_t)cid * 64 + wp * 8);
+          pa1 = *reinterpret_cast<const int4*>(s.P + (int64_t)cid * 64 + wp * 8 + 4);
+        }
+      }
+      const uint32_t lw[4] = {lv8.x, lv8.y, lv8.z, lv8.w};
+      const int32_t pw[8] = {pa0.x, pa0.y, pa0.z, pa0.w, pa1.x, pa1.y, pa1.z, pa1.w};
+      const int32_t none = info == INT32_MIN ? -2 : -1;
+#pragma unroll
       for (int k = 0; k < 8; ++k) {
-        const int l = wp * 8 + k;
-        if (l >= s.nlanes) break;
-        int32_t lv = info == INT32_MIN ? -2 : -1, pa = lv;
-        if ((vis >> l) & 1ull) {
-          lv = (int32_t)s.L[(int64_t)cid * 64 + l] + s.lane[l].base + add;
-          pa = add ? fixed_parent : s.P[(int64_t)cid * 64 + l];
-        }
-        if (in) {
-          s.outl[l][v] = lv;
-          s.outp[l][v] = pa;
-        }
+        if (k >= nl || !in) continue;
+        const bool r = (vis >> k) & 1u;
+        const int32_t lk = (int32_t)((lw[k >> 1] >> (16 * (k & 1))) & 0xFFFFu);
+        ol[k][v] = r ? lk + base[k] + add : none;
+        op[k][v] = r ? (add ? fixed_parent : pw[k]) : none;
       }
     }
   }
@@ -521,28 +604,39 @@ void free_batch_mem(gt_graph* g) {
   g->batch_slots_alloc = 0;
 }
 
-// Grows the handle's pool of lane-word storage (7 buffers per 64 roots, core-sized) to
-// `need` slots.
+void slot_sizes(const gt_graph* g, size_t sz[SLOT_BUFS]) {
+  const size_t nc = (size_t)std::max<int64_t>(g->core.n, 1);
+  const size_t q = 2 * (size_t)(g->core.nnz / BATCH_CHUNK) + 64;  // chunks of long frontier adjacencies
+  const size_t v[SLOT_BUFS] = {8 * nc, 8 * nc, 8 * nc, 256 * nc, 128 * nc, 4 * nc, 4 * nc, 8 * q};
+  for (int i = 0; i < SLOT_BUFS; ++i) sz[i] = v[i];
+}
+
+size_t slot_bytes(const gt_graph* g) {
+  size_t sz[SLOT_BUFS], t = 0;
+  slot_sizes(g, sz);
+  for (int i = 0; i < SLOT_BUFS; ++i) t += sz[i];
+  return t;
+}
+
+// Grows the handle's pool of lane-word storage (SLOT_BUFS buffers per 64 roots) to `need`
+// slots.
 int ensure_slots(gt_graph* g, int need) {
-  const int64_t nc = std::max<int64_t>(g->core.n, 1);
+  size_t sz[SLOT_BUFS];
+  slot_sizes(g, sz);
   while (g->batch_slots_alloc < need) {
-    void* p[7];
-    const size_t sz[7] = {8 * (size_t)nc, 8 * (size_t)nc, 8 * (size_t)nc, 256 * (size_t)nc, 128 * (size_t)nc,
-                          4 * (size_t)nc, 4 * (size_t)nc};
-    for (int i = 0; i < 7; ++i) {
+    void* p[SLOT_BUFS];
+    for (int i = 0; i < SLOT_BUFS; ++i) {
       int rc = device_malloc(g, &p[i], sz[i]);
       if (rc) {
         for (int j = 0; j < i; ++j) cudaFree(p[j]);
         return rc;
       }
     }
-    for (int i = 0; i < 7; ++i) g->batch_mem.push_back(p[i]);
+    for (int i = 0; i < SLOT_BUFS; ++i) g->batch_mem.push_back(p[i]);
     g->batch_slots_alloc += 1;
   }
   return GT_OK;
 }
-
-size_t slot_bytes(const gt_graph* g) { return (size_t)std::max<int64_t>(g->core.n, 1) * (8 * 3 + 256 + 128 + 8); }
 
 void batch_ctx_free(BatchCtx* c) {
   if (!c) return;
@@ -565,7 +659,7 @@ int batch_launch(BatchCtx* ctx, const SlotSpec* specs, int nspecs, int sm_share,
   const int ns = nspecs;
   const size_t t_slots = (sizeof(SlotDev) * ns + 255) & ~(size_t)255;
   const size_t t_ctl = (sizeof(SlotCtl) * ns + 255) & ~(size_t)255;
-  const size_t bytes = t_slots + t_ctl + 256 + sizeof(ResolveSeg) * ns * 2 + 256;
+  const size_t bytes = t_slots + t_ctl + 256;
   if (ctx->cap < ns) {
     if (ctx->dev) cudaFree(ctx->dev);
     ctx->dev = nullptr;
@@ -597,6 +691,10 @@ int batch_launch(BatchCtx* ctx, const SlotSpec* specs, int nspecs, int sm_share,
     d.anchor_vid = g->anchor_vid;
     d.up = g->up;
     d.old2core = g->old2core;
+    d.lanes = g->batch_lane;
+    d.items = g->batch_item;
+    d.n_lanes = g->n_batch_lane;
+    d.n_items = g->n_batch_item;
     d.visit = (uint64_t*)sp.mem[0];
     d.front[0] = (uint64_t*)sp.mem[1];
     d.front[1] = (uint64_t*)sp.mem[2];
@@ -604,6 +702,7 @@ int batch_launch(BatchCtx* ctx, const SlotSpec* specs, int nspecs, int sm_share,
     d.L = (uint16_t*)sp.mem[4];
     d.fl[0] = (int32_t*)sp.mem[5];
     d.fl[1] = (int32_t*)sp.mem[6];
+    d.q = (uint64_t*)sp.mem[7];
     d.nlanes = sp.nlanes;
     d.alpha = g->tuning.batch_alpha;
     d.beta = g->tuning.batch_beta;
@@ -623,16 +722,16 @@ int batch_launch(BatchCtx* ctx, const SlotSpec* specs, int nspecs, int sm_share,
     cudaMemsetAsync(d.visit, 0, 8 * nc, st);
     cudaMemsetAsync(d.front[0], 0, 8 * nc, st);
     cudaMemsetAsync(d.front[1], 0, 8 * nc, st);
+    cudaMemsetAsync(d.P, 0xFF, 256 * nc, st);  // parents taken by atomicMin start above every id
   }
   char* base = (char*)ctx->dev;
   SlotDev* d_slots = (SlotDev*)base;
   SlotCtl* d_ctl = (SlotCtl*)(base + t_slots);
   BatchCtl* d_bc = (BatchCtl*)(base + t_slots + t_ctl);
-  ResolveSeg* d_seg = (ResolveSeg*)(base + t_slots + t_ctl + 256);
   int rc = cuda_fail(cudaMemcpyAsync(d_slots, hs.data(), sizeof(SlotDev) * ns, cudaMemcpyHostToDevice, st), "slots");
   if (rc) return rc;
   std::vector<SlotCtl> hc(ns);
-  for (int i = 0; i < ns; ++i) hc[i] = SlotCtl{{0, 0}, 0, 0, DIR_TD, 0, 0};
+  for (int i = 0; i < ns; ++i) hc[i] = SlotCtl{{0, 0}, 0, 0, 0, DIR_TD, 0, 0};
   const BatchCtl hb{0u, 0, ns, 0};
   cudaMemcpyAsync(d_ctl, hc.data(), sizeof(SlotCtl) * ns, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(d_bc, &hb, sizeof(hb), cudaMemcpyHostToDevice, st);
@@ -673,7 +772,6 @@ int batch_launch(BatchCtx* ctx, const SlotSpec* specs, int nspecs, int sm_share,
     cudaMemcpyAsync(dseg, segs.data(), sizeof(ResolveSeg) * segs.size(), cudaMemcpyHostToDevice, st);
     for (int h = 0; h < maxh; ++h) batch_resolve<<<dim3(64, ns), BT, 0, st>>>(d_slots, dseg + (size_t)h * ns, ns);
   }
-  (void)d_seg;
   cudaMemcpyAsync(ctx->h_err, &d_bc->err, sizeof(int), cudaMemcpyDeviceToHost, st);
   return cuda_fail(cudaGetLastError(), "batch kernels");
 }
@@ -709,7 +807,7 @@ int run_batch(gt_graph* const* graphs, int ngraphs, const int64_t* roots, const 
     for (int k = 0; k < nsg; ++k) {
       SlotSpec sp;
       sp.g = g;
-      sp.mem = &g->batch_mem[7 * k];
+      sp.mem = &g->batch_mem[(size_t)SLOT_BUFS * k];
       sp.nlanes = std::min(64, r - 64 * k);
       sp.roots = roots + ro + 64 * k;
       const size_t off = lanes_p.size();

@@ -271,6 +271,25 @@ __global__ void list_anchors(int64_t nc, const uint8_t* __restrict__ aflag, cons
   }
 }
 
+// Work lists of the batched traversal: short adjacencies one per lane, long ones in chunks.
+__global__ void batch_work_count(int64_t nc, const int64_t* __restrict__ crow, uint8_t* __restrict__ short_flag,
+                                 int32_t* __restrict__ nchunks) {
+  for (int64_t v = gtid(); v < nc; v += gthreads()) {
+    const int64_t d = crow[v + 1] - crow[v];
+    short_flag[v] = d > 0 && d <= BATCH_LANE_DEG;
+    nchunks[v] = d > BATCH_LANE_DEG ? (int32_t)((d + BATCH_CHUNK - 1) / BATCH_CHUNK) : 0;
+  }
+}
+
+__global__ void batch_work_fill(int64_t nc, const uint8_t* __restrict__ short_flag, const int32_t* __restrict__ lpos,
+                                const int32_t* __restrict__ nchunks, const int64_t* __restrict__ ipos,
+                                int32_t* __restrict__ lanes, uint64_t* __restrict__ items) {
+  for (int64_t v = gtid(); v < nc; v += gthreads()) {
+    if (short_flag[v]) lanes[lpos[v]] = (int32_t)v;
+    for (int32_t c = 0; c < nchunks[v]; ++c) items[ipos[v] + c] = ((uint64_t)v << 32) | (uint32_t)c;
+  }
+}
+
 // vinfo: core id for core vertices; -2 - (anchor index of up) for tree vertices hanging
 // from a core vertex; INT32_MIN for tree vertices hanging from another tree vertex
 // (resolved height by height, listed through rflag); -1 for the rest (zero-degree
@@ -419,6 +438,8 @@ void free_graph(gt_graph* g) {
   cudaFree(g->anchor_cid);
   cudaFree(g->anchor_vid);
   cudaFree(g->anchor_out);
+  cudaFree(g->batch_lane);
+  cudaFree(g->batch_item);
   cudaFree(g->new2old);
   cudaFree(g->old2core);
   free_batch_mem(g);
@@ -607,6 +628,33 @@ int build_graph(gt_graph* g, const int64_t* edges, int64_t m, int64_t n, cudaStr
   TRY(device_malloc(g, (void**)&cv.col, sizeof(int32_t) * std::max<int64_t>(cv.nnz, 1)));
   if (nc > 0) core_fill<<<gw, BT, 0, s>>>(g->row, g->col, is_core, g->new2old, g->old2core, nc, cv.row, cv.col);
   TRYC(cudaGetLastError(), "core csr");
+
+  // ---- batched traversal work lists
+  {
+    uint8_t* sflag;
+    int32_t *lpos, *nch;
+    int64_t* ipos;
+    const int64_t nc1 = std::max<int64_t>(nc, 1);
+    TRY(tmp_malloc(tmp, (void**)&sflag, nc1));
+    TRY(tmp_malloc(tmp, (void**)&lpos, sizeof(int32_t) * (nc + 1)));
+    TRY(tmp_malloc(tmp, (void**)&nch, sizeof(int32_t) * nc1));
+    TRY(tmp_malloc(tmp, (void**)&ipos, sizeof(int64_t) * (nc + 1)));
+    if (nc > 0) batch_work_count<<<grid_for(g, nc), BT, 0, s>>>(nc, cv.row, sflag, nch);
+    TRY(scan_u8_to_i32(sflag, lpos, nc, s, d_scan, scan_bytes));
+    TRY(scan_i32_to_i64(nch, ipos, nc, s, d_scan, scan_bytes));
+    int32_t nl = 0;
+    int64_t ni = 0;
+    TRYC(cudaMemcpyAsync(&nl, lpos + nc, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "readback");
+    TRYC(cudaMemcpyAsync(&ni, ipos + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s), "readback");
+    TRYC(cudaStreamSynchronize(s), "sync");
+    g->n_batch_lane = nl;
+    g->n_batch_item = ni;
+    TRY(device_malloc(g, (void**)&g->batch_lane, sizeof(int32_t) * std::max<int64_t>(nl, 1)));
+    TRY(device_malloc(g, (void**)&g->batch_item, sizeof(uint64_t) * std::max<int64_t>(ni, 1)));
+    if (nc > 0)
+      batch_work_fill<<<grid_for(g, nc), BT, 0, s>>>(nc, sflag, lpos, nch, ipos, g->batch_lane, g->batch_item);
+    TRYC(cudaGetLastError(), "batch work lists");
+  }
 
   // ---- a4: anchors and tree layout
   uint8_t* aflag;

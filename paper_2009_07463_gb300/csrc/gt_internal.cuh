@@ -20,6 +20,11 @@ constexpr int BU_CHUNK_WORDS = 128;     // bitmap words one warp takes per step 
 // can give each vertex the right amount of the machine: packed lanes (bin 0), a warp
 // (bin 1), a CTA (bin 2) or the whole grid (bin 3).
 constexpr int NBINS = 4;
+// Batched traversal work split: core vertices of degree <= BATCH_LANE_DEG are scanned by
+// one lane each; longer adjacencies are cut into chunks of BATCH_CHUNK entries, each a
+// work item for a warp.
+constexpr int BATCH_LANE_DEG = 32;
+constexpr int BATCH_CHUNK = 2048;
 
 // Per-traversal control block in device memory. Kernels read the direction and buffer
 // selectors from here, so the level loop can run without the host (CUDA graph with a
@@ -107,6 +112,11 @@ struct gt_graph {
   int32_t* anchor_cid = nullptr;  // anchor -> core id
   int32_t* anchor_vid = nullptr;  // anchor -> vertex id
   uint64_t* anchor_out = nullptr; // per traversal: (level + 1) << 32 | vertex id, for its tree children
+  // batched traversal work lists over the core (built with the graph)
+  int64_t n_batch_lane = 0;
+  int32_t* batch_lane = nullptr;    // core vertices of degree 1..BATCH_LANE_DEG
+  int64_t n_batch_item = 0;
+  uint64_t* batch_item = nullptr;   // (core id << 32) | chunk index, for longer adjacencies
   int32_t* new2old = nullptr;   // core id -> vertex id
   int32_t* old2core = nullptr;  // vertex id -> core id or -1
   int32_t* resolve_list = nullptr;  // tree vertices whose up is a tree vertex, by height desc
@@ -126,7 +136,7 @@ struct gt_graph {
   std::vector<double> step_ms;
   cudaEvent_t phase_events[4] = {nullptr, nullptr, nullptr, nullptr};
   double phase_ms[3] = {-1.0, -1.0, -1.0};  // start, level loop, output (time_kernels)
-  // batched traversal: per-slot device storage (7 buffers per slot) and the slot table
+  // batched traversal: per-slot device storage (SLOT_BUFS buffers per slot) and the slot table
   std::vector<void*> batch_mem;
   int batch_slots_alloc = 0;
   gt::BatchCtx* batch_ctx = nullptr;
@@ -165,7 +175,7 @@ int run_bfs(gt_graph* g, View& v, bool et, int64_t root, int32_t* parent, int32_
 // One lane word (up to 64 roots of one graph) of a batched launch.
 struct SlotSpec {
   gt_graph* g;
-  void* const* mem;         // 7 slot buffers from the graph's pool (ensure_slots)
+  void* const* mem;         // SLOT_BUFS slot buffers from the graph's pool (ensure_slots)
   int nlanes;
   const int64_t* roots;     // nlanes roots
   int32_t* const* outp;     // nlanes parent arrays (device, n entries)
@@ -174,6 +184,10 @@ struct SlotSpec {
 int run_batch(gt_graph* const* graphs, int ngraphs, const int64_t* roots, const int32_t* roots_per_graph,
               int32_t* const* parent, int32_t* const* level, cudaStream_t s);
 int ensure_slots(gt_graph* g, int need);
+// A lane word's device buffers: visit, front x 2, parents, levels, frontier lists x 2,
+// top-down chunk queue.
+constexpr int SLOT_BUFS = 8;
+void slot_sizes(const gt_graph* g, size_t sz[SLOT_BUFS]);
 size_t slot_bytes(const gt_graph* g);
 // Enqueues a whole batched traversal on `st` (cooperative kernel on sm_share SMs' worth of
 // CTAs, 0 = all); batch_status() reads its outcome once the stream has passed it.

@@ -49,7 +49,7 @@ struct Query {
 };
 
 struct SlotBuf {
-  void* p[7];
+  void* p[SLOT_BUFS];
 };
 
 struct GraphEntry {
@@ -165,11 +165,10 @@ void CUDART_CB on_flight_done(void* arg) {
 bool grow_slots(gt_server* s, GraphEntry& ge) {
   const size_t sb = slot_bytes(ge.g);
   if (s->used_bytes + (int64_t)sb > s->cfg.hbm_budget_bytes) return false;
-  const int64_t nc = std::max<int64_t>(ge.g->core.n, 1);
-  const size_t sz[7] = {8 * (size_t)nc, 8 * (size_t)nc, 8 * (size_t)nc, 256 * (size_t)nc, 128 * (size_t)nc,
-                        4 * (size_t)nc, 4 * (size_t)nc};
+  size_t sz[SLOT_BUFS];
+  slot_sizes(ge.g, sz);
   SlotBuf b{};
-  for (int i = 0; i < 7; ++i) {
+  for (int i = 0; i < SLOT_BUFS; ++i) {
     if (cudaMalloc(&b.p[i], sz[i]) != cudaSuccess) {
       cudaGetLastError();
       for (int j = 0; j < i; ++j) cudaFree(b.p[j]);
@@ -538,7 +537,7 @@ GT_API int gt_serve_destroy(gt_server_t s) {
   for (auto& c : s->ctxs) batch_ctx_free(&c);
   for (auto& ge : s->graphs)
     for (auto& b : ge.slots)
-      for (int i = 0; i < 7; ++i) cudaFree(b.p[i]);
+      for (int i = 0; i < SLOT_BUFS; ++i) cudaFree(b.p[i]);
   for (auto& kv : s->tickets) delete kv.second;
   delete s;
   return GT_OK;

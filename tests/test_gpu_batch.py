@@ -130,3 +130,22 @@ def test_batch_equals_single_calls_and_repeats(torch):
         for i, r in enumerate(roots[:16]):
             p, l = g.bfs(r)
             assert np.array_equal(L[i], l) and np.array_equal(P[i], p), f"rep {rep} root {r}"
+
+
+@pytest.mark.parametrize("batch_alpha", [1, 14, 1 << 30])
+def test_batch_hubs_span_several_chunks(torch, batch_alpha):
+    # four hubs of degree ~5000 (adjacencies cut into several work chunks, so parents are
+    # merged across chunks) over a sparse random graph; both directions forced in turn
+    rng = np.random.default_rng(31)
+    n = 12000
+    pairs = [graphgen.uniform_edges(n, 3 * n, seed=32)]
+    for h in range(4):
+        nb = rng.choice(np.arange(4, n), size=5000, replace=False)
+        pairs.append(np.stack([np.full(nb.size, h), nb], axis=1))
+    e = np.concatenate(pairs).astype(np.int64)
+    og = OracleGraph(e, n)
+    g = gt.gt_graph_build(e, n)
+    g.set_tuning(batch_alpha=batch_alpha)
+    roots = [0, 1, 2, 3] + graphgen.pick_roots(33, n, 60, og.degree()).tolist()
+    (P,), (L,) = run_batch(torch, [g], [roots])
+    check_rows(P, L, og, roots, f"hubs alpha={batch_alpha}")
