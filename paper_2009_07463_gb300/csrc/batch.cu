@@ -266,6 +266,23 @@ __device__ __forceinline__ void td_push(const SlotDev& s, uint64_t f, int32_t vo
   }
 }
 
+// Per-launch reset of every slot's lane words (visit, both fronts) and of the staged
+// parents (all ones: parents taken by atomicMin start above every id).
+__global__ void batch_clear(SlotDev* slots, int nslots) {
+  for (int si = 0; si < nslots; ++si) {
+    const SlotDev& s = slots[si];
+    const int64_t nc = s.nc > 0 ? s.nc : 1;
+    for (int64_t i = gtid(); i < nc; i += gthreads()) {
+      s.visit[i] = 0ull;
+      s.front[0][i] = 0ull;
+      s.front[1][i] = 0ull;
+    }
+    uint4* P = reinterpret_cast<uint4*>(s.P);
+    const int64_t np = nc * 16;  // 64 int32 per vertex
+    for (int64_t i = gtid(); i < np; i += gthreads()) P[i] = make_uint4(~0u, ~0u, ~0u, ~0u);
+  }
+}
+
 __global__ void batch_init(SlotDev* slots, SlotCtl* sctl, int nslots) {
   // one thread per (slot, lane): walk the root to its core vertex (Alg. 9) and seed it
   const int sidx = blockIdx.x;
@@ -640,15 +657,34 @@ int ensure_slots(gt_graph* g, int need) {
 
 void batch_ctx_free(BatchCtx* c) {
   if (!c) return;
+  if (c->exec) cudaGraphExecDestroy(c->exec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->dev) cudaFree(c->dev);
-  if (c->seg_dev) cudaFree(c->seg_dev);
+  if (c->stage) cudaFreeHost(c->stage);
   if (c->h_err) cudaFreeHost(c->h_err);
-  c->dev = nullptr;
-  c->seg_dev = nullptr;
-  c->h_err = nullptr;
-  c->cap = 0;
-  c->seg_cap = 0;
+  *c = BatchCtx{};
 }
+
+namespace {
+
+// Enqueues the kernels of one batched traversal on `st` (tables already in `dev`).
+void enqueue_batch(SlotDev* d_slots, SlotCtl* d_ctl, BatchCtl* d_bc, ResolveSeg* d_seg, int ns, int maxh, int grid,
+                   int ogrid, int* h_err, const void* stage, void* dev, size_t bytes, cudaStream_t st) {
+  cudaMemcpyAsync(dev, stage, bytes, cudaMemcpyHostToDevice, st);
+  batch_clear<<<ogrid, BT, 0, st>>>(d_slots, ns);
+  batch_lanes<<<ns, 64, 0, st>>>(d_slots, ns);
+  batch_init<<<ns, 64, 0, st>>>(d_slots, d_ctl, ns);
+  int32_t cl = 0;
+  int nsl = ns;
+  void* kargs[] = {(void*)&d_slots, (void*)&d_ctl, (void*)&nsl, (void*)&d_bc, (void*)&cl};
+  cudaLaunchCooperativeKernel((void*)batch_run, dim3(grid), dim3(BT), kargs, 0, st);
+  batch_output<<<ogrid, BT, 0, st>>>(d_slots, ns);
+  batch_fixup<<<ns, 64, 0, st>>>(d_slots, ns);
+  for (int h = 0; h < maxh; ++h) batch_resolve<<<dim3(64, ns), BT, 0, st>>>(d_slots, d_seg + (size_t)h * ns, ns);
+  cudaMemcpyAsync(h_err, &d_bc->err, sizeof(int), cudaMemcpyDeviceToHost, st);
+}
+
+}  // namespace
 
 int batch_launch(BatchCtx* ctx, const SlotSpec* specs, int nspecs, int sm_share, cudaStream_t st) {
   if (nspecs <= 0) return GT_OK;
@@ -657,23 +693,36 @@ int batch_launch(BatchCtx* ctx, const SlotSpec* specs, int nspecs, int sm_share,
     return GT_EINVAL;
   }
   const int ns = nspecs;
+  int maxh = 0;
+  for (int i = 0; i < ns; ++i) maxh = std::max(maxh, specs[i].g->resolve_heights);
+  // table layout: slots | slot control | batch control | resolution segments
   const size_t t_slots = (sizeof(SlotDev) * ns + 255) & ~(size_t)255;
   const size_t t_ctl = (sizeof(SlotCtl) * ns + 255) & ~(size_t)255;
-  const size_t bytes = t_slots + t_ctl + 256;
-  if (ctx->cap < ns) {
+  const size_t t_bc = 256;
+  const size_t bytes = t_slots + t_ctl + t_bc + sizeof(ResolveSeg) * (size_t)ns * std::max(maxh, 1);
+  if (ctx->cap_bytes < bytes) {
+    // the captured graph points at the old buffers: drop it with them
+    if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
+    ctx->exec = nullptr;
     if (ctx->dev) cudaFree(ctx->dev);
-    ctx->dev = nullptr;
+    if (ctx->stage) cudaFreeHost(ctx->stage);
+    ctx->dev = ctx->stage = nullptr;
+    ctx->cap_bytes = 0;
     int rc = cuda_fail(cudaMalloc(&ctx->dev, bytes), "batch table");
+    if (rc == GT_OK) rc = cuda_fail(cudaHostAlloc(&ctx->stage, bytes, cudaHostAllocDefault), "batch staging");
     if (rc) return rc;
-    ctx->cap = ns;
+    ctx->cap_bytes = bytes;
   }
   if (!ctx->h_err) {
     int rc = cuda_fail(cudaHostAlloc((void**)&ctx->h_err, sizeof(int) * 4, cudaHostAllocDefault), "pinned status");
     if (rc) return rc;
   }
   ctx->h_err[0] = 0;
-  std::vector<SlotDev> hs(ns);
-  int maxh = 0;
+  char* hb = (char*)ctx->stage;
+  SlotDev* hs = (SlotDev*)hb;
+  SlotCtl* hc = (SlotCtl*)(hb + t_slots);
+  BatchCtl* hbc = (BatchCtl*)(hb + t_slots + t_ctl);
+  ResolveSeg* hseg = (ResolveSeg*)(hb + t_slots + t_ctl + t_bc);
   gt_graph* g0 = specs[0].g;
   for (int i = 0; i < ns; ++i) {
     const SlotSpec& sp = specs[i];
@@ -717,63 +766,53 @@ int batch_launch(BatchCtx* ctx, const SlotSpec* specs, int nspecs, int sm_share,
       d.outp[l] = sp.outp[l];
       d.outl[l] = sp.outl[l];
     }
-    maxh = std::max(maxh, g->resolve_heights);
-    const size_t nc = (size_t)std::max<int64_t>(g->core.n, 1);
-    cudaMemsetAsync(d.visit, 0, 8 * nc, st);
-    cudaMemsetAsync(d.front[0], 0, 8 * nc, st);
-    cudaMemsetAsync(d.front[1], 0, 8 * nc, st);
-    cudaMemsetAsync(d.P, 0xFF, 256 * nc, st);  // parents taken by atomicMin start above every id
+    hc[i] = SlotCtl{{0, 0}, 0, 0, 0, DIR_TD, 0, 0};
+    // heights are processed top down; each slot walks its own graph's segments
+    for (int h = 0; h < maxh; ++h) {
+      ResolveSeg sg{g->resolve_list, g->resolve_up, 0, 0};
+      if (h < g->resolve_heights) {
+        sg.b = g->resolve_ptr_host[h];
+        sg.e = g->resolve_ptr_host[h + 1];
+      }
+      hseg[(size_t)h * ns + i] = sg;
+    }
   }
+  *hbc = BatchCtl{0u, 0, ns, 0};
   char* base = (char*)ctx->dev;
   SlotDev* d_slots = (SlotDev*)base;
   SlotCtl* d_ctl = (SlotCtl*)(base + t_slots);
   BatchCtl* d_bc = (BatchCtl*)(base + t_slots + t_ctl);
-  int rc = cuda_fail(cudaMemcpyAsync(d_slots, hs.data(), sizeof(SlotDev) * ns, cudaMemcpyHostToDevice, st), "slots");
-  if (rc) return rc;
-  std::vector<SlotCtl> hc(ns);
-  for (int i = 0; i < ns; ++i) hc[i] = SlotCtl{{0, 0}, 0, 0, 0, DIR_TD, 0, 0};
-  const BatchCtl hb{0u, 0, ns, 0};
-  cudaMemcpyAsync(d_ctl, hc.data(), sizeof(SlotCtl) * ns, cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(d_bc, &hb, sizeof(hb), cudaMemcpyHostToDevice, st);
-  batch_lanes<<<ns, 64, 0, st>>>(d_slots, ns);
-  batch_init<<<ns, 64, 0, st>>>(d_slots, d_ctl, ns);
+  ResolveSeg* d_seg = (ResolveSeg*)(base + t_slots + t_ctl + t_bc);
   int nb_per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_per_sm, batch_run, BT, 0);
   const int share = std::max(1, std::min(sm_share > 0 ? sm_share : g0->launch.sms, g0->launch.sms));
   const int grid = std::max(1, std::min(nb_per_sm, 4)) * share;
-  int32_t cl = 0;
-  int nsl = ns;
-  void* kargs[] = {(void*)&d_slots, (void*)&d_ctl, (void*)&nsl, (void*)&d_bc, (void*)&cl};
-  rc = cuda_fail(cudaLaunchCooperativeKernel((void*)batch_run, dim3(grid), dim3(BT), kargs, 0, st), "batch launch");
-  if (rc) return rc;
-  batch_output<<<share * 16, BT, 0, st>>>(d_slots, ns);
-  batch_fixup<<<ns, 64, 0, st>>>(d_slots, ns);
-  if (maxh > 0) {
-    // heights are processed top down; each slot walks its own graph's segments
-    std::vector<ResolveSeg> segs((size_t)ns * maxh);
-    for (int h = 0; h < maxh; ++h)
-      for (int i = 0; i < ns; ++i) {
-        gt_graph* g = specs[i].g;
-        ResolveSeg sg{g->resolve_list, g->resolve_up, 0, 0};
-        if (h < g->resolve_heights) {
-          sg.b = g->resolve_ptr_host[h];
-          sg.e = g->resolve_ptr_host[h + 1];
-        }
-        segs[(size_t)h * ns + i] = sg;
-      }
-    if (ctx->seg_cap < (int64_t)segs.size()) {
-      if (ctx->seg_dev) cudaFree(ctx->seg_dev);
-      ctx->seg_dev = nullptr;
-      rc = cuda_fail(cudaMalloc(&ctx->seg_dev, sizeof(ResolveSeg) * segs.size()), "resolve table");
+  const int ogrid = share * 16;
+  const bool same = ctx->exec && ctx->key_ns == ns && ctx->key_maxh == maxh && ctx->key_grid == grid &&
+                    ctx->key_ogrid == ogrid && ctx->key_bytes == bytes;
+  if (!same) {
+    if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
+    ctx->exec = nullptr;
+    if (!ctx->cap_stream) {
+      int rc = cuda_fail(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking), "capture stream");
       if (rc) return rc;
-      ctx->seg_cap = (int64_t)segs.size();
     }
-    ResolveSeg* dseg = (ResolveSeg*)ctx->seg_dev;
-    cudaMemcpyAsync(dseg, segs.data(), sizeof(ResolveSeg) * segs.size(), cudaMemcpyHostToDevice, st);
-    for (int h = 0; h < maxh; ++h) batch_resolve<<<dim3(64, ns), BT, 0, st>>>(d_slots, dseg + (size_t)h * ns, ns);
+    int rc = cuda_fail(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal), "batch capture");
+    if (rc) return rc;
+    enqueue_batch(d_slots, d_ctl, d_bc, d_seg, ns, maxh, grid, ogrid, ctx->h_err, ctx->stage, ctx->dev, bytes,
+                  ctx->cap_stream);
+    cudaGraph_t graph = nullptr;
+    rc = cuda_fail(cudaStreamEndCapture(ctx->cap_stream, &graph), "batch capture end");
+    if (rc == GT_OK) rc = cuda_fail(cudaGraphInstantiate(&ctx->exec, graph, 0), "batch graph instantiate");
+    if (graph) cudaGraphDestroy(graph);
+    if (rc) return rc;
+    ctx->key_ns = ns;
+    ctx->key_maxh = maxh;
+    ctx->key_grid = grid;
+    ctx->key_ogrid = ogrid;
+    ctx->key_bytes = bytes;
   }
-  cudaMemcpyAsync(ctx->h_err, &d_bc->err, sizeof(int), cudaMemcpyDeviceToHost, st);
-  return cuda_fail(cudaGetLastError(), "batch kernels");
+  return cuda_fail(cudaGraphLaunch(ctx->exec, st), "batch graph launch");
 }
 
 int batch_status(const BatchCtx* ctx) {

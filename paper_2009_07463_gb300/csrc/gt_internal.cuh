@@ -80,14 +80,19 @@ struct LaunchCfg {
   int grid = 608;
 };
 
-// A reusable launch context of the batched traversal: device slot table and a pinned
-// status word read back after the launch completes.
+// A reusable launch context of the batched traversal. The launch tables (slot
+// descriptors, control words, resolution segments) are written into pinned staging memory
+// and uploaded by the first node of a captured CUDA graph of the whole launch; the graph
+// is kept and replayed while its shape (slots, resolution heights, grid) stays the same.
 struct BatchCtx {
-  void* dev = nullptr;
-  int cap = 0;
-  void* seg_dev = nullptr;
-  int64_t seg_cap = 0;
-  int* h_err = nullptr;
+  void* dev = nullptr;       // device copy of the tables
+  void* stage = nullptr;     // pinned host staging of the tables
+  size_t cap_bytes = 0;
+  int* h_err = nullptr;      // pinned status word, read back by the graph's last node
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  int key_ns = -1, key_maxh = -1, key_grid = -1, key_ogrid = -1;
+  size_t key_bytes = 0;
 };
 
 }  // namespace gt
