@@ -56,9 +56,14 @@ def parse():
     ap.add_argument("--trace-out", default="")
     ap.add_argument("--launch-mode", default="graph", choices=["graph", "host"],
                     help="host: one launch per kernel (lets ncu see every kernel; slower)")
-    ap.add_argument("--workload", default="et", choices=["et", "batch", "serve"],
+    ap.add_argument("--workload", default="et", choices=["et", "batch", "serve", "study"],
                     help="et: single-root edge-tree BFS (the headline line); batch: 64-root lane words "
-                         "on scale 24 plus a mixed 32-graph batch; serve: Poisson queries on 12 resident graphs")
+                         "on scale 24 plus a mixed 32-graph batch; serve: Poisson queries on 12 resident graphs; "
+                         "study: scale / edge-factor / MH sweeps and the gain ablation, edge-tree vs plain")
+    ap.add_argument("--study-scales", default="20,22,24,26,27")
+    ap.add_argument("--study-efs", default="8,16,32")
+    ap.add_argument("--study-mhs", default="0,1,2,-1")
+    ap.add_argument("--study-roots", type=int, default=32)
     ap.add_argument("--serve-rates", default="4000,16000,48000")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-policies", default="adaptive,batched,single",
@@ -276,6 +281,8 @@ def main():
         return run_batch_workload(a, rank, local)
     if a.workload == "serve":
         return run_serve_workload(a, rank, local)
+    if a.workload == "study":
+        return run_study_workload(a, rank, local)
 
     # the oracle leg is spawned before the first GPU call
     oracle = None
@@ -447,13 +454,17 @@ def main():
         out["roofline"] = {"bound": "hbm", "kernel": "bfs_bu_gather+bfs_bu_scan", "achieved": round(bu_gbs, 1), "peak": peak,
                            "peak_source": peak_src, "unit": "GB/s", "frac": round(bu_gbs / peak, 4),
                            "traffic": trf, "launches": bu_n,
+                           "dram_achieved": round(trf / (bu_t / max(bu_n, 1) * 1e-3) / 1e9, 1) if trf and bu_t > 0 else None,
+                           "dram_frac": round(trf / (bu_t / max(bu_n, 1) * 1e-3) / 1e9 / peak, 4) if trf and bu_t > 0 else None,
                            "bytes_per_launch": round(bu_b / max(bu_n, 1)),
                            "ms_per_launch": round(bu_t / max(bu_n, 1), 4),
                            "share_of_step_time": round(bu_t / (bu_t + td_t), 3) if bu_t + td_t > 0 else None,
                            "td": {"achieved": round(td_gbs, 1), "frac": round(td_gbs / peak, 4), "launches": td_n,
                                   "ms_per_launch": round(td_t / max(td_n, 1), 4)},
                            "how": "achieved = algorithmic bytes from per-level work counts / kernel duration from "
-                                  "CUDA events around each launch (host-driven kernel-timing pass, same roots)"}
+                                  "CUDA events around each launch (host-driven kernel-timing pass, same roots); "
+                                  "dram_achieved = ncu DRAM bytes per bottom-up step (profiles/bfs_bu_traffic.txt, "
+                                  "same kernel source) / the same duration"}
         if a.trace_out:
             json.dump({"roots": roots, "counted": counted, "timed": timed, "tuples": tuples,
                        "run_ms": run_ms, "phases": phases}, open(a.trace_out, "w"))
@@ -713,6 +724,126 @@ def run_serve_workload(a, rank, local):
                                   "Poisson arrivals", "hbm_budget_gib": 48, "streams": 2, "max_batch_roots": 128,
                       "window_us": 100, "seconds_per_rate": a.serve_seconds},
            "rates": results}
+    print(json.dumps(out), flush=True)
+
+
+def run_study_workload(a, rank, local):
+    """Sweeps and ablation around the headline (edge-tree vs plain direction-optimizing BFS,
+    harmonic-mean GTEPS over the first --study-roots seeded roots, each root timed alone with
+    CUDA events after one warm-up pass):
+      scales   R-MAT scales --study-scales at edge factor 16, MH = 0;
+      efs      edge factors --study-efs at --scale;
+      mhs      maximum tree heights --study-mhs at --scale, edge factor 16 (class counts,
+               tree height, build time beside the GTEPS);
+      ablation at --scale: plain BFS; plain BFS after dropping zero-degree vertices (ids
+               relabelled in order); the core BFS alone (root mapping + level loop, no
+               edge-tree resolution or output pass: timing only); full edge-tree BFS."""
+    import numpy as np
+    import torch
+
+    import graphgen
+    import paper_2009_07463_gb300 as gt
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    nroots = a.study_roots
+
+    def make(scale, ef, mh):
+        n, m = 1 << scale, ef << scale
+        e = torch.empty((m, 2), dtype=torch.int64, device=dev)
+        graphgen.rmat_edges_device(e.data_ptr(), scale, m, seed=a.seed, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        g = gt.gt_graph_build(e, n, mh=mh, stream=stream)
+        torch.cuda.synchronize()
+        return g, e, n, time.time() - t0
+
+    def timed(fn, roots, tuples, n):
+        p = torch.empty(n, dtype=torch.int32, device=dev)
+        l = torch.empty(n, dtype=torch.int32, device=dev)
+        for r in roots:  # warm-up
+            fn(r, p, l, stream=stream)
+        evs = []
+        for r in roots:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(r, p, l, stream=stream)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        ms = [x.elapsed_time(y) for x, y in evs]
+        return round(hmean([t / (x * 1e-3) / 1e9 for t, x in zip(tuples, ms)]), 2)
+
+    def et_vs_plain(scale, ef, mh):
+        g, e, n, build_s = make(scale, ef, mh)
+        roots = graphgen.pick_roots(a.root_seed, n, nroots, g.degree()).tolist()
+        lvl = torch.empty(n, dtype=torch.int32, device=dev)
+        par = torch.empty(n, dtype=torch.int32, device=dev)
+        tuples = []
+        for r in roots:
+            g.bfs(r, par, lvl, stream=stream)
+            tuples.append(gt.gt_count_traversed(e, lvl, stream=stream))
+        st = g.stats()
+        out = {"scale": scale, "edgefactor": ef, "mh": mh, "et_gteps": timed(g.bfs, roots, tuples, n),
+               "plain_gteps": timed(g.bfs_plain, roots, tuples, n), "core_fraction": round(st["n_core"] / n, 4),
+               "classes_CI_CE_TI_TL_VZ": st["n_class"], "tree_height": st["height"], "build_s": round(build_s, 3)}
+        out["et_over_plain"] = round(out["et_gteps"] / out["plain_gteps"], 3) if out["plain_gteps"] else None
+        return g, e, n, roots, tuples, out
+
+    res = {"scales": [], "efs": [], "mhs": []}
+    for sc in [int(x) for x in a.study_scales.split(",") if x]:
+        g, e, *_, out = et_vs_plain(sc, 16, 0)
+        res["scales"].append(out)
+        print(json.dumps({"study": "scale", **out}), flush=True)
+        del g, e
+        torch.cuda.empty_cache()
+    for ef in [int(x) for x in a.study_efs.split(",") if x]:
+        g, e, *_, out = et_vs_plain(a.scale, ef, 0)
+        res["efs"].append(out)
+        print(json.dumps({"study": "edgefactor", **out}), flush=True)
+        del g, e
+        torch.cuda.empty_cache()
+    for mh in [int(x) for x in a.study_mhs.split(",") if x]:
+        g, e, *_, out = et_vs_plain(a.scale, 16, mh)
+        res["mhs"].append(out)
+        print(json.dumps({"study": "mh", **out}), flush=True)
+        del g, e
+        torch.cuda.empty_cache()
+    # ablation (Fig. 5): plain -> plain without zero-degree vertices -> core BFS alone -> full
+    g, e, n, roots, tuples, full = et_vs_plain(a.scale, 16, 0)
+    keep = torch.from_numpy(g.degree() > 0).to(dev)
+    newid = torch.cumsum(keep.to(torch.int64), 0) - 1
+    n2 = int(keep.sum().item())
+    e2 = newid[e]
+    g2 = gt.gt_graph_build(e2, n2, stream=stream)
+    del e2
+    torch.cuda.empty_cache()
+    roots2 = newid[torch.tensor(roots, device=dev)].tolist()
+    rmzero = timed(g2.bfs_plain, roots2, tuples, n2)
+    g2.free()
+    g.set_tuning(time_kernels=1)
+    p = torch.empty(n, dtype=torch.int32, device=dev)
+    lv = torch.empty(n, dtype=torch.int32, device=dev)
+    core_ms = []
+    for r in roots:
+        g.bfs(r, p, lv, stream=stream)
+    for r in roots:
+        g.bfs(r, p, lv, stream=stream)
+        t = g.timing()
+        core_ms.append(t["start_ms"] + t["loop_ms"])
+    g.set_tuning(time_kernels=0)
+    core_only = round(hmean([t / (x * 1e-3) / 1e9 for t, x in zip(tuples, core_ms)]), 2)
+    abl = {"scale": a.scale, "plain_gteps": full["plain_gteps"], "plain_without_zero_degree_gteps": rmzero,
+           "core_bfs_only_gteps": core_only, "edge_tree_bfs_gteps": full["et_gteps"],
+           "note": "core BFS alone = root mapping + level loop without resolution or output (timing only)"}
+    res["ablation"] = abl
+    print(json.dumps({"study": "ablation", **abl}), flush=True)
+    out = {"metric": "edge-tree vs plain BFS, harmonic-mean GTEPS (sweeps and ablation)", "value": full["et_gteps"],
+           "unit": "GTEPS", "n_gpus": 1, "higher_is_better": True, "dtype": "int32", "data": "synthetic",
+           "config": {"workload": "study: R-MAT scale / edge factor / MH sweeps and the gain ablation",
+                      "roots": nroots, "scale": a.scale}, "study": res}
     print(json.dumps(out), flush=True)
 
 
