@@ -142,12 +142,42 @@ __device__ __forceinline__ void stage_push(StageQ& sq, bool disc, int32_t w, int
   __syncwarp();
 }
 
-// One frontier edge (v -> w) of a top-down step; packed = (L+1) << 32 | v.
-__device__ __forceinline__ bool td_visit(uint64_t* state, const uint32_t* vis, int32_t w, uint64_t packed) {
-  if ((vis[w >> 5] >> (w & 31)) & 1u) return false;  // visited before this level (may lag: only a filter)
-  if (state[w] <= packed) return false;               // already as good (values only decrease)
-  const unsigned long long old = atomicMin((unsigned long long*)&state[w], (unsigned long long)packed);
-  return old == UNVISITED;
+constexpr int TDK = 4;  // top-down edges a lane keeps in flight
+
+// TDK frontier edges (v -> w) of one lane at once (w < 0: no edge; packed = (L+1) << 32 |
+// v): the visited-bit filter (visited before this level; may lag, so only a filter), the
+// state pre-check (values only decrease, so an entry already as good needs no atomic),
+// the atomicMin and the degree load are each issued for all edges together, so their
+// latencies overlap. disc[t]: this edge replaced "unvisited", i.e. discovered w.
+__device__ __forceinline__ void td_visit_k(const BfsArgs& a, const uint32_t* vis, const int32_t (&w)[TDK],
+                                           const uint64_t (&packed)[TDK], bool (&disc)[TDK],
+                                           int64_t (&wd)[TDK]) {
+  uint32_t vw[TDK];
+#pragma unroll
+  for (int t = 0; t < TDK; ++t) vw[t] = w[t] >= 0 ? vis[w[t] >> 5] : ~0u;
+  bool cand[TDK];
+  uint64_t st[TDK];
+#pragma unroll
+  for (int t = 0; t < TDK; ++t) {
+    cand[t] = w[t] >= 0 && !((vw[t] >> (w[t] & 31)) & 1u);
+    st[t] = cand[t] ? a.state[w[t]] : 0ull;
+  }
+  unsigned long long old[TDK];
+#pragma unroll
+  for (int t = 0; t < TDK; ++t) {
+    cand[t] = cand[t] && st[t] > packed[t];
+    old[t] = cand[t] ? atomicMin((unsigned long long*)&a.state[w[t]], (unsigned long long)packed[t]) : 0ull;
+  }
+#pragma unroll
+  for (int t = 0; t < TDK; ++t) disc[t] = cand[t] && old[t] == UNVISITED;
+  int64_t r0[TDK], r1[TDK];
+#pragma unroll
+  for (int t = 0; t < TDK; ++t) {
+    r0[t] = disc[t] ? a.row[w[t]] : 0;
+    r1[t] = disc[t] ? a.row[w[t] + 1] : 0;
+  }
+#pragma unroll
+  for (int t = 0; t < TDK; ++t) wd[t] = r1[t] - r0[t];
 }
 
 // Adds per-thread counts into the control block with one atomic per CTA and counter.
@@ -178,26 +208,31 @@ __device__ __forceinline__ void block_commit(const BfsArgs& a, int64_t n_found, 
 }
 
 // Walks the adjacency entries [s, e) of frontier vertex v with `stride` lanes starting at
-// lane offset `first`; all lanes of the warp take part in every step.
+// lane offset `first`, TDK windows per step; all lanes of the warp take part in every step.
 __device__ __forceinline__ void td_edges(const BfsArgs& a, uint32_t* vis, int nxt, int32_t v, uint64_t hi,
                                          int64_t s, int64_t e, int64_t first, int64_t stride, int64_t& nf,
                                          int64_t& mf, StageQ& sq) {
   const uint64_t packed = hi | orig_of(a, v);
-  for (int64_t k0 = s + first; k0 < e; k0 += stride) {
-    const int64_t k = k0 + (threadIdx.x & 31);
-    bool disc = false;
-    int32_t w = 0;
-    int64_t wd = 0;
-    if (k < e) {
-      w = a.col[k];
-      disc = td_visit(a.state, vis, w, packed);
-      if (disc) {
-        wd = a.row[w + 1] - a.row[w];
-        ++nf;
-        mf += wd;
-      }
+  for (int64_t k0 = s + first; k0 < e; k0 += stride * TDK) {
+    int32_t w[TDK];
+    uint64_t pk[TDK];
+    bool disc[TDK];
+    int64_t wd[TDK];
+#pragma unroll
+    for (int t = 0; t < TDK; ++t) {
+      const int64_t k = k0 + t * stride + (threadIdx.x & 31);
+      w[t] = k < e ? a.col[k] : -1;
+      pk[t] = packed;
     }
-    stage_push(sq, disc, w, wd, a, nxt, a.ctl->next_bin_n);
+    td_visit_k(a, vis, w, pk, disc, wd);
+#pragma unroll
+    for (int t = 0; t < TDK; ++t) {
+      if (disc[t]) {
+        ++nf;
+        mf += wd[t];
+      }
+      stage_push(sq, disc[t], w[t], wd[t], a, nxt, a.ctl->next_bin_n);
+    }
   }
 }
 
@@ -267,27 +302,35 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) bfs_td(BfsArgs a) {
       __syncthreads();
       const int64_t E = s_pre[cnt];
       if (blockIdx.x == 0 && threadIdx.x == 0) examined += E;
-      for (int64_t c0 = gw * 32; c0 < E; c0 += nw * 32) {
-        const int64_t off = c0 + lane;
-        bool disc = false;
-        int32_t w = 0;
-        int64_t wd = 0;
-        if (off < E) {
-          int lo = 0, hi2 = cnt - 1;  // largest idx with s_pre[idx] <= off
-          while (lo < hi2) {
-            const int mid = (lo + hi2 + 1) >> 1;
-            if (s_pre[mid] <= off) lo = mid; else hi2 = mid - 1;
-          }
-          const int32_t v = s_v[lo];
-          w = a.col[s_beg[lo] + (off - s_pre[lo])];
-          disc = td_visit(a.state, vis, w, hi | (uint32_t)v);
-          if (disc) {
-            wd = a.row[w + 1] - a.row[w];
-            ++nf;
-            mf += wd;
+      for (int64_t c0 = gw * 32 * TDK; c0 < E; c0 += nw * 32 * TDK) {
+        int32_t w[TDK];
+        uint64_t pk[TDK];
+        bool disc[TDK];
+        int64_t wd[TDK];
+#pragma unroll
+        for (int t = 0; t < TDK; ++t) {
+          const int64_t off = c0 + 32 * t + lane;
+          w[t] = -1;
+          pk[t] = 0;
+          if (off < E) {
+            int lo = 0, hi2 = cnt - 1;  // largest idx with s_pre[idx] <= off
+            while (lo < hi2) {
+              const int mid = (lo + hi2 + 1) >> 1;
+              if (s_pre[mid] <= off) lo = mid; else hi2 = mid - 1;
+            }
+            w[t] = a.col[s_beg[lo] + (off - s_pre[lo])];
+            pk[t] = hi | (uint32_t)s_v[lo];
           }
         }
-        stage_push(sq, disc, w, wd, a, nxt, ctl->next_bin_n);
+        td_visit_k(a, vis, w, pk, disc, wd);
+#pragma unroll
+        for (int t = 0; t < TDK; ++t) {
+          if (disc[t]) {
+            ++nf;
+            mf += wd[t];
+          }
+          stage_push(sq, disc[t], w[t], wd[t], a, nxt, ctl->next_bin_n);
+        }
       }
       __syncthreads();
     }
@@ -340,30 +383,35 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) bfs_td(BfsArgs a) {
       const int32_t total = __shfl_sync(FULL, incl, 31);
       const int32_t excl = incl - sd;
       if (lane == 0) examined += total;
-      for (int32_t r0 = 0; r0 < total; r0 += 32) {
-        const int32_t idx = r0 + lane;
-        int owner = 0;
+      for (int32_t r0 = 0; r0 < total; r0 += 32 * TDK) {
+        int32_t w[TDK];
+        uint64_t pk[TDK];
+        bool disc[TDK];
+        int64_t wd[TDK];
 #pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-          const int cand = owner + step;
-          if (__shfl_sync(FULL, excl, cand) <= idx) owner = cand;
-        }
-        const int32_t ov = __shfl_sync(FULL, vo, owner);
-        const int64_t ors = __shfl_sync(FULL, rs, owner);
-        const int32_t oex = __shfl_sync(FULL, excl, owner);
-        bool disc = false;
-        int32_t w = 0;
-        int64_t wd = 0;
-        if (idx < total) {
-          w = a.col[ors + (idx - oex)];
-          disc = td_visit(a.state, vis, w, hi | (uint32_t)ov);
-          if (disc) {
-            wd = a.row[w + 1] - a.row[w];
-            ++nf;
-            mf += wd;
+        for (int t = 0; t < TDK; ++t) {
+          const int32_t idx = r0 + 32 * t + lane;
+          int owner = 0;
+#pragma unroll
+          for (int step = 16; step > 0; step >>= 1) {
+            const int cand = owner + step;
+            if (__shfl_sync(FULL, excl, cand) <= idx) owner = cand;
           }
+          const int32_t ov = __shfl_sync(FULL, vo, owner);
+          const int64_t ors = __shfl_sync(FULL, rs, owner);
+          const int32_t oex = __shfl_sync(FULL, excl, owner);
+          w[t] = idx < total ? a.col[ors + (idx - oex)] : -1;
+          pk[t] = hi | (uint32_t)ov;
         }
-        stage_push(sq, disc, w, wd, a, nxt, ctl->next_bin_n);
+        td_visit_k(a, vis, w, pk, disc, wd);
+#pragma unroll
+        for (int t = 0; t < TDK; ++t) {
+          if (disc[t]) {
+            ++nf;
+            mf += wd[t];
+          }
+          stage_push(sq, disc[t], w[t], wd[t], a, nxt, ctl->next_bin_n);
+        }
       }
     }
   }
