@@ -202,17 +202,19 @@ class Clocks:
 # ---- roofline helpers ---------------------------------------------------------------------
 
 def bu_bytes(lv: dict, n_core: int, visited_before: int, nwords: int) -> float:
-    """Algorithmic bytes of one bottom-up step: read + write the visited bitmap, one int64
-    row offset per unvisited vertex, 4 B per adjacency entry examined plus its 1-bit
-    visited probe, and 12 B (state + queue) per vertex found."""
+    """Algorithmic bytes of one bottom-up step, per-unit figures of the method: the visited
+    bitmap once (N_core / 8 B), a 16 B row-offset pair per unvisited vertex, 4 B per
+    adjacency entry examined plus its 1-bit frontier probe, 8 B (level, parent) per vertex
+    found."""
     unvisited = n_core - visited_before
-    return 8.0 * nwords + 8.0 * unvisited + 4.125 * lv["examined"] + 12.0 * lv["discovered"]
+    return 4.0 * nwords + 16.0 * unvisited + 4.125 * lv["examined"] + 8.0 * lv["discovered"]
 
 
 def td_bytes(lv: dict) -> float:
-    """Top-down step: 16 B of row offsets per frontier vertex, 4 B per frontier edge plus its
-    1-bit visited probe, 28 B per vertex found (8 B state, 4 B queue, 16 B of its offsets)."""
-    return 16.0 * lv["frontier"] + 4.125 * lv["frontier_edges"] + 28.0 * lv["discovered"]
+    """Top-down step: a 16 B row-offset pair per frontier vertex, 4 B per frontier edge read
+    plus 4 B for the state check of the vertex it reaches, 12 B (level, parent, queue
+    entry) per vertex found."""
+    return 16.0 * lv["frontier"] + 8.0 * lv["frontier_edges"] + 12.0 * lv["discovered"]
 
 
 def traffic_from_profiles(kernel: str) -> float | None:

@@ -101,8 +101,8 @@ int autotune(gt_graph* g, int nsample, uint64_t seed, cudaStream_t s, gt_tuning*
     bool batch;
   };
   const std::vector<Knob> knobs = {
-      {&gt_tuning::alpha, {4, 8, 14, 24, 48}, false},
-      {&gt_tuning::beta, {8, 16, 24, 48, 96}, false},
+      {&gt_tuning::alpha, {8, 14, 20, 32, 48}, false},
+      {&gt_tuning::beta, {24, 64, 128, 256, 512}, false},
       {&gt_tuning::td_warp_min, {8, 16, 32, 64}, false},
       {&gt_tuning::td_cta_min, {128, 256, 512, 1024}, false},
       {&gt_tuning::td_grid_min, {1024, 2048, 4096, 16384}, false},
