@@ -305,8 +305,7 @@ __global__ void batch_init(SlotDev* slots, SlotCtl* sctl, int nslots) {
   }
 }
 
-__global__ void __launch_bounds__(BT) batch_run(SlotDev* slots, SlotCtl* sctl, int nslots, BatchCtl* bc,
-                                                int32_t count_levels) {
+__global__ void __launch_bounds__(BT) batch_run(SlotDev* slots, SlotCtl* sctl, int nslots, BatchCtl* bc) {
   __shared__ int s_cur[MAX_SLOTS_SMEM], s_dir[MAX_SLOTS_SMEM], s_done[MAX_SLOTS_SMEM], s_it[MAX_SLOTS_SMEM];
   __shared__ int64_t s_ncur[MAX_SLOTS_SMEM];
   const int lane = threadIdx.x & 31;
@@ -457,7 +456,6 @@ __global__ void __launch_bounds__(BT) batch_run(SlotDev* slots, SlotCtl* sctl, i
     }
     if (!grid_barrier(bc, gen)) return;
     if (*(volatile int*)&bc->live <= 0) return;
-    (void)count_levels;
   }
 }
 
@@ -674,9 +672,8 @@ void enqueue_batch(SlotDev* d_slots, SlotCtl* d_ctl, BatchCtl* d_bc, ResolveSeg*
   batch_clear<<<ogrid, BT, 0, st>>>(d_slots, ns);
   batch_lanes<<<ns, 64, 0, st>>>(d_slots, ns);
   batch_init<<<ns, 64, 0, st>>>(d_slots, d_ctl, ns);
-  int32_t cl = 0;
   int nsl = ns;
-  void* kargs[] = {(void*)&d_slots, (void*)&d_ctl, (void*)&nsl, (void*)&d_bc, (void*)&cl};
+  void* kargs[] = {(void*)&d_slots, (void*)&d_ctl, (void*)&nsl, (void*)&d_bc};
   cudaLaunchCooperativeKernel((void*)batch_run, dim3(grid), dim3(BT), kargs, 0, st);
   batch_output<<<ogrid, BT, 0, st>>>(d_slots, ns);
   batch_fixup<<<ns, 64, 0, st>>>(d_slots, ns);
