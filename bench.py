@@ -60,6 +60,9 @@ def parse():
                     help="et: single-root edge-tree BFS (the headline line); batch: 64-root lane words "
                          "on scale 24 plus a mixed 32-graph batch; serve: Poisson queries on 12 resident graphs; "
                          "study: scale / edge-factor / MH sweeps and the gain ablation, edge-tree vs plain")
+    ap.add_argument("--batch-scale", type=int, default=24, help="batch workload: R-MAT scale of the 64-root part")
+    ap.add_argument("--batch-parts", default="single,mixed", help="batch workload parts: single (one graph) and/or mixed")
+    ap.add_argument("--no-batch-autotune", action="store_true", help="batch workload: keep default tuning")
     ap.add_argument("--study-scales", default="20,22,24,26,27")
     ap.add_argument("--study-efs", default="8,16,32")
     ap.add_argument("--study-mhs", default="0,1,2,-1")
@@ -232,15 +235,16 @@ def traffic_from_profiles(kernel: str) -> float | None:
 
 
 def launches_of(trace: list[dict]) -> int:
-    """Kernels one gt_bfs launches: reset, start, per level select + step kernels + decide,
-    output and the root-walk fix-up (resolve passes are absent at MH = 0 but for K2 tops).
-    Step kernels: top-down 1; bottom-up 2 (gather, scan), plus a mark after a top-down step."""
-    k = 4
+    """Kernels one gt_bfs launches: reset, start, per level the step kernels + decide, the
+    anchor gather, output and the root-walk fix-up (resolve passes are absent at MH = 0 but
+    for K2 tops). Step kernels: top-down 1; bottom-up 2 (gather, scan), plus a mark after a
+    top-down step."""
+    k = 5
     if not trace:
-        return k + 3
+        return k + 2
     prev = None
     for t in trace:
-        k += 2  # select, decide
+        k += 1  # decide
         if t["direction"] == "td":
             k += 1
         else:
@@ -535,7 +539,7 @@ def _make_graph(gt, graphgen, torch, kind, a_, seed, dev):
 
 
 def run_batch_workload(a, rank, local):
-    """Batch workload: 64 roots in one lane word on R-MAT scale 24, and a mixed batch of 32 graphs
+    """Batch workload: 64 roots in one lane word on R-MAT scale 24 (--batch-scale), and a mixed batch of 32 graphs
     (R-MAT scales 14-22, uniform graphs of average degree 16), 64 roots each, every batch in
     one persistent launch with autotuned parameters; against the same roots run one at a
     time with gt_bfs. Queries/s and GTEPS-equivalent (traversed tuples / time)."""
@@ -564,7 +568,8 @@ def run_batch_workload(a, rank, local):
         graphs, roots, tuples = [], [], []
         for i, (kind, arg) in enumerate(specs):
             g, e = _make_graph(gt, graphgen, torch, kind, arg, 100 + i, dev)
-            g.autotune(nsample=4, seed=7)
+            if not a.no_batch_autotune:
+                g.autotune(nsample=4, seed=7)
             r = graphgen.pick_roots(3 + i, g.n, 64, g.degree()).tolist()
             lv = torch.empty(g.n, dtype=torch.int32, device=dev)
             pa = torch.empty(g.n, dtype=torch.int32, device=dev)
@@ -599,14 +604,19 @@ def run_batch_workload(a, rank, local):
             g.free()
         torch.cuda.empty_cache()
 
-    measure([("rmat", 24)], "rmat_s24_64_roots")
-    mixed = [("rmat", 14 + (i % 9)) for i in range(24)] + [("uniform", (1 << (15 + (i % 6)), 16)) for i in range(8)]
-    measure(mixed, "mixed_32_graphs_64_roots_each")
+    parts = [x for x in a.batch_parts.split(",") if x]
+    if "single" in parts:
+        measure([("rmat", a.batch_scale)], f"rmat_s{a.batch_scale}_64_roots")
+    if "mixed" in parts:
+        mixed = [("rmat", 14 + (i % 9)) for i in range(24)] + [("uniform", (1 << (15 + (i % 6)), 16)) for i in range(8)]
+        measure(mixed, "mixed_32_graphs_64_roots_each")
+    head = res.get("mixed_32_graphs_64_roots_each") or next(iter(res.values()))
     out = {"metric": "batched BFS queries/s (64-root lane words, one persistent launch)",
-           "value": res["mixed_32_graphs_64_roots_each"]["batch_qps"], "unit": "queries/s", "n_gpus": 1,
+           "value": head["batch_qps"], "unit": "queries/s", "n_gpus": 1,
            "higher_is_better": True, "dtype": "int32", "data": "synthetic",
-           "config": {"workload": "batch: rmat s24 x 64 roots; 32 mixed graphs (rmat s14-22, uniform deg 16) x 64 roots",
-                      "autotuned": True, "cuda_graph": "each batched launch is one captured graph, replayed"}, "results": res}
+           "config": {"workload": f"batch: rmat s{a.batch_scale} x 64 roots; 32 mixed graphs (rmat s14-22, uniform "
+                                  "deg 16) x 64 roots", "parts": parts, "autotuned": not a.no_batch_autotune,
+                      "cuda_graph": "each batched launch is one captured graph, replayed"}, "results": res}
     print(json.dumps(out), flush=True)
 
 

@@ -732,7 +732,10 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) bfs_bu_scan(BfsArgs a) {
 // pick the next direction by the frontier-size rule of Beamer et al. (the paper's
 // reference [12]; Alg. 1 calls it is_top_down_direction): top-down -> bottom-up when
 // m_f * alpha > m_u, bottom-up -> top-down when n_f * beta < n and the frontier shrank.
-__global__ void bfs_decide(BfsArgs a, cudaGraphConditionalHandle h_loop, int use_handles) {
+__device__ __forceinline__ unsigned step_kind(const BfsCtl* c);
+
+__global__ void bfs_decide(BfsArgs a, cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_dir,
+                           int use_handles) {
   BfsCtl* c = a.ctl;
   if (!c->done) {
     const int L = c->level, dir = c->dir;
@@ -781,7 +784,10 @@ __global__ void bfs_decide(BfsArgs a, cudaGraphConditionalHandle h_loop, int use
     c->bu_hash = c->need_mark && nn <= HASH_CAP;
     c->dir = nd;
   }
-  if (use_handles) cudaGraphSetConditional(h_loop, c->done ? 0u : 1u);
+  if (use_handles) {
+    cudaGraphSetConditional(h_loop, c->done ? 0u : 1u);
+    if (!c->done) cudaGraphSetConditional(h_dir, step_kind(c));  // routes the next iteration
+  }
 }
 
 // Which step kernels run next: 0 top-down, 1 bottom-up, 2 mark + bottom-up,
@@ -791,10 +797,6 @@ __device__ __forceinline__ unsigned step_kind(const BfsCtl* c) {
   return c->need_mark ? (c->bu_hash ? 4u : 2u) : 1u;
 }
 
-// First node of each loop iteration: routes the switch to the step now due.
-__global__ void bfs_select(BfsCtl* c, cudaGraphConditionalHandle h_dir) {
-  cudaGraphSetConditional(h_dir, step_kind(c));
-}
 
 // Clears the traversal state: state = UNVISITED, visited bitmap 0 except the padding
 // bits past n (kept set so no scan ever takes them for unvisited vertices).
@@ -1049,10 +1051,10 @@ unsigned host_step_kind(int dir, int need_mark, int need_queue, int bu_hash) {
 }
 
 // Builds the CUDA graph of the level loop for one view:
-//   WHILE(loop) { select -> SWITCH(kind) { 0: td | 1: gather, scan | 2: mark, gather, scan |
-//                                          3: queue, td } -> decide }
-// The while handle (created on the top graph, default 1) is set by decide; the switch
-// handle belongs to the body graph, which holds its node, and is set by select.
+//   WHILE(loop) { SWITCH(kind) { 0: td | 1: gather, scan | 2: mark, gather, scan |
+//                                3: queue, td | 4: mark, gather, scan (frontier set) } -> decide }
+// Both handles are created on the top graph with a launch default (loop: 1; kind: the
+// first step of a fresh traversal); decide sets them for the next iteration.
 int build_loop_graph(gt_graph* g, const View& v, cudaGraphExec_t* out) {
   const BfsArgs a = make_args(v, g->tuning);
   const int grid = g->launch.grid;
@@ -1063,8 +1065,14 @@ int build_loop_graph(gt_graph* g, const View& v, cudaGraphExec_t* out) {
     if (rc == GT_OK) rc = cuda_fail(e, what);
   };
   fail(cudaGraphCreate(&graph, 0), "graph create");
+  // both handles live on the top graph and are reset at every launch: the loop runs, and
+  // the first step is the one a fresh traversal starts with (top-down, or bottom-up when
+  // forced); afterwards decide routes each next iteration
+  const unsigned first_kind = g->tuning.force_direction == 2 ? 1u : 0u;
   cudaGraphConditionalHandle h_loop = 0, h_dir = 0;
   if (rc == GT_OK) fail(cudaGraphConditionalHandleCreate(&h_loop, graph, 1, cudaGraphCondAssignDefault), "handle");
+  if (rc == GT_OK)
+    fail(cudaGraphConditionalHandleCreate(&h_dir, graph, first_kind, cudaGraphCondAssignDefault), "handle");
   if (rc == GT_OK) fail(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "stream");
   cudaGraph_t body = nullptr;
   if (rc == GT_OK) {
@@ -1077,18 +1085,6 @@ int build_loop_graph(gt_graph* g, const View& v, cudaGraphExec_t* out) {
     fail(cudaGraphAddNode(&loop, graph, nullptr, nullptr, 0, &np), "while node");
     if (rc == GT_OK) body = np.conditional.phGraph_out[0];
   }
-  if (rc == GT_OK) fail(cudaGraphConditionalHandleCreate(&h_dir, body, 0, 0), "handle");
-  cudaGraphNode_t sel = nullptr;
-  if (rc == GT_OK) {
-    cudaKernelNodeParams kp{};
-    BfsCtl* ctl = a.ctl;
-    void* args[] = {(void*)&ctl, (void*)&h_dir};
-    kp.func = (void*)bfs_select;
-    kp.gridDim = dim3(1);
-    kp.blockDim = dim3(1);
-    kp.kernelParams = args;
-    fail(cudaGraphAddKernelNode(&sel, body, nullptr, 0, &kp), "select node");
-  }
   cudaGraph_t branch[NKINDS] = {};
   cudaGraphNode_t sw = nullptr;
   if (rc == GT_OK) rc = prepare_kernels();
@@ -1098,7 +1094,7 @@ int build_loop_graph(gt_graph* g, const View& v, cudaGraphExec_t* out) {
     np.conditional.handle = h_dir;
     np.conditional.type = cudaGraphCondTypeSwitch;
     np.conditional.size = NKINDS;
-    fail(cudaGraphAddNode(&sw, body, &sel, nullptr, 1, &np), "switch node");
+    fail(cudaGraphAddNode(&sw, body, nullptr, nullptr, 0, &np), "switch node");
     if (rc == GT_OK)
       for (int i = 0; i < NKINDS; ++i) branch[i] = np.conditional.phGraph_out[i];
   }
@@ -1113,7 +1109,7 @@ int build_loop_graph(gt_graph* g, const View& v, cudaGraphExec_t* out) {
     cudaKernelNodeParams kp{};
     int use = 1;
     BfsArgs ac = a;
-    void* args[] = {(void*)&ac, (void*)&h_loop, (void*)&use};
+    void* args[] = {(void*)&ac, (void*)&h_loop, (void*)&h_dir, (void*)&use};
     kp.func = (void*)bfs_decide;
     kp.gridDim = dim3(1);
     kp.blockDim = dim3(1);
@@ -1168,7 +1164,7 @@ int run_level_loop(gt_graph* g, View& v, int which, cudaStream_t s) {
       cudaEventRecord(g->step_events[2 * guard + 1], s);
       ++timed_steps;
     }
-    bfs_decide<<<1, 1, 0, s>>>(a, none, 0);
+    bfs_decide<<<1, 1, 0, s>>>(a, none, none, 0);
     rc = cuda_fail(cudaGetLastError(), "level launch");
     if (rc != GT_OK) return rc;
   }
@@ -1359,7 +1355,7 @@ extern "C" GT_API int gt_bfs_csr_noalloc(const int64_t* row, const int32_t* col,
     if (rc) return rc;
     if (h.done) break;
     launch_step(h.dir == DIR_TD ? (h.need_queue ? 3 : 0) : (h.need_mark ? 2 : 1), a, grid, s);
-    bfs_decide<<<1, 1, 0, s>>>(a, 0, 0);
+    bfs_decide<<<1, 1, 0, s>>>(a, 0, 0, 0);
     rc = cuda_fail(cudaGetLastError(), "level launch");
     if (rc) return rc;
   }
