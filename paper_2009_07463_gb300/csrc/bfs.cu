@@ -768,7 +768,7 @@ __global__ void bfs_decide(BfsArgs a, cudaGraphConditionalHandle h_loop, cudaGra
     if (dir == DIR_BU) c->vcur ^= 1;
     c->level = L + 1;
     int nd = dir;
-    if (nn == 0) {
+    if (nn == 0 || c->m_u == 0) {  // no frontier, or no unvisited vertex with an edge left
       c->done = 1;
     } else if (c->force == 1) {
       nd = DIR_TD;

@@ -179,9 +179,15 @@ def test_trace_directions(torch_cuda):
     g.set_tuning(count_work=1)
     bfs_dev(torch, g, r)
     tr = g.trace()
-    assert tr and tr[0]["frontier"] == 1 and tr[-1]["discovered"] == 0
+    assert tr and tr[0]["frontier"] == 1
     assert {t["direction"] for t in tr} == {"td", "bu"}  # the switch does fire on R-MAT
     assert all(t["examined"] >= 0 for t in tr)
+    # plain BFS on the whole graph: every reached vertex but the root is discovered on
+    # exactly one traced level, and the loop stops once no unvisited edge is left
+    lv, _ = bfs_dev(torch, g, r, plain=True)
+    tp = g.trace()
+    assert sum(t["discovered"] for t in tp) + 1 == int((lv >= 0).sum())
+    assert all(t["unvisited_edges"] > 0 for t in tp[1:])
     g.set_tuning(force_direction=1)
     bfs_dev(torch, g, r)
     assert {t["direction"] for t in g.trace()} == {"td"}
