@@ -8,10 +8,11 @@
 // value wins, i.e. level L+1 with the smallest frontier neighbour as parent, and the
 // one thread that replaced UNVISITED enqueues the vertex. Bottom-up (Alg. 1 BOTTOM-UP,
 // with the block search of Alg. 5): unvisited vertices are gathered from the visited
-// bitmap in 128-bit words; each scans its ascending adjacency and stops at the first
-// visited neighbour (visited before this level means "in the frontier" for an
-// unvisited vertex), which is the smallest one. Both directions therefore give the
-// same levels and min-id parents, whatever the switch does.
+// bitmap in 128-bit words; each scans its ascending adjacency (the first three entries
+// from a 16-byte per-vertex prefix record) and stops at the first visited neighbour
+// (visited before this level means "in the frontier" for an unvisited vertex), which is
+// the smallest one. Both directions therefore give the same levels and min-id parents,
+// whatever the switch does.
 #include <algorithm>
 #include <mutex>
 #include <string>
