@@ -149,3 +149,28 @@ def test_batch_hubs_span_several_chunks(torch, batch_alpha):
     roots = [0, 1, 2, 3] + graphgen.pick_roots(33, n, 60, og.degree()).tolist()
     (P,), (L,) = run_batch(torch, [g], [roots])
     check_rows(P, L, og, roots, f"hubs alpha={batch_alpha}")
+
+
+def test_batch_graph_replay_takes_new_roots_and_outputs(torch):
+    # the batched launch is a captured graph replayed while its shape is unchanged: a second
+    # call with other roots and other output buffers must use them; a call with another
+    # shape (more lane words) recaptures
+    n = 1 << 14
+    e = graphgen.rmat_edges(14, 16, seed=21)
+    og = OracleGraph(e, n)
+    g = gt.gt_graph_build(e, n)
+    cand = graphgen.pick_roots(22, n, 200, og.degree()).tolist()
+    for roots in (cand[:64], cand[64:128], cand[:150], cand[150:200]):
+        (P,), (L,) = run_batch(torch, [g], [roots])
+        check_rows(P, L, og, roots, f"replay {len(roots)} roots")
+
+
+def test_batch_rejects_too_many_lane_words(torch):
+    n = 1 << 10
+    e = graphgen.rmat_edges(10, 16, seed=23)
+    g = gt.gt_graph_build(e, n)
+    roots = [0] * (64 * 256 + 1)  # one lane word more than one launch takes
+    p = torch.empty((len(roots), n), dtype=torch.int32, device="cuda")
+    with pytest.raises(gt.GtError) as ei:
+        gt.gt_bfs_batch([g], [roots], [p], [p])
+    assert ei.value.code == gt.GT_EINVAL
