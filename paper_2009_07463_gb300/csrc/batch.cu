@@ -833,17 +833,39 @@ int run_batch(gt_graph* const* graphs, int ngraphs, const int64_t* roots, const 
   for (int gi = 0; gi < ngraphs; ++gi) total_words += (rpg[gi] + 63) / 64;
   lanes_p.reserve((size_t)total_words * 64);
   lanes_l.reserve((size_t)total_words * 64);
+  // lane words per graph (a graph may be listed more than once): grow every pool first, so
+  // no pointer into a pool is taken before the pool stops growing
+  std::vector<std::pair<gt_graph*, int>> need;
+  for (int gi = 0; gi < ngraphs; ++gi) {
+    const int nsg = (rpg[gi] + 63) / 64;
+    bool seen = false;
+    for (auto& u : need)
+      if (u.first == graphs[gi]) {
+        u.second += nsg;
+        seen = true;
+      }
+    if (!seen) need.emplace_back(graphs[gi], nsg);
+  }
+  for (auto& u : need) {
+    int rc = ensure_slots(u.first, u.second);
+    if (rc) return rc;
+    u.second = 0;  // from here: lane words handed out so far
+  }
   int64_t ro = 0;
   for (int gi = 0; gi < ngraphs; ++gi) {
     gt_graph* g = graphs[gi];
     const int r = rpg[gi];
     const int nsg = (r + 63) / 64;
-    int rc = ensure_slots(g, nsg);
-    if (rc) return rc;
+    int first = 0;
+    for (auto& u : need)
+      if (u.first == g) {
+        first = u.second;
+        u.second += nsg;
+      }
     for (int k = 0; k < nsg; ++k) {
       SlotSpec sp;
       sp.g = g;
-      sp.mem = &g->batch_mem[(size_t)SLOT_BUFS * k];
+      sp.mem = &g->batch_mem[(size_t)SLOT_BUFS * (first + k)];
       sp.nlanes = std::min(64, r - 64 * k);
       sp.roots = roots + ro + 64 * k;
       const size_t off = lanes_p.size();

@@ -174,3 +174,16 @@ def test_batch_rejects_too_many_lane_words(torch):
     with pytest.raises(gt.GtError) as ei:
         gt.gt_bfs_batch([g], [roots], [p], [p])
     assert ei.value.code == gt.GT_EINVAL
+
+
+def test_batch_same_graph_twice(torch):
+    # one handle listed twice takes separate lane-word storage for each list
+    n = 1 << 13
+    e = graphgen.rmat_edges(13, 16, seed=25)
+    og = OracleGraph(e, n)
+    g = gt.gt_graph_build(e, n)
+    cand = graphgen.pick_roots(26, n, 100, og.degree()).tolist()
+    r1, r2 = cand[:70], cand[70:]
+    P, L = run_batch(torch, [g, g], [r1, r2])
+    check_rows(P[0], L[0], og, r1, "first list")
+    check_rows(P[1], L[1], og, r2, "second list")
