@@ -125,6 +125,22 @@ def _ptr(x) -> int:
     raise TypeError(f"cannot take a pointer of {type(x)}")
 
 
+def _out(x, count: int, what: str) -> int:
+    """Pointer of an int32 output buffer, after checking that an array or tensor holds at
+    least `count` contiguous int32 entries (raw integer pointers are taken as given)."""
+    if x is None or isinstance(x, int):
+        return _ptr(x)
+    if isinstance(x, np.ndarray):
+        ok = x.dtype == np.int32 and x.flags.c_contiguous and x.size >= count
+    elif hasattr(x, "numel"):
+        ok = str(x.dtype) == "torch.int32" and x.is_contiguous() and x.numel() >= count
+    else:
+        raise TypeError(f"{what}: cannot take a pointer of {type(x)}")
+    if not ok:
+        raise ValueError(f"{what}: need a contiguous int32 buffer of at least {count} entries")
+    return _ptr(x)
+
+
 def _stream(s) -> int:
     if s is None:
         try:
@@ -207,7 +223,7 @@ class Graph:
             parent = np.empty(self.n, dtype=np.int32)
             level = np.empty(self.n, dtype=np.int32)
         f = lib().gt_bfs_plain if plain else lib().gt_bfs
-        _check(f(self._h, int(root), _ptr(parent), _ptr(level), _stream(stream)),
+        _check(f(self._h, int(root), _out(parent, self.n, "parent"), _out(level, self.n, "level"), _stream(stream)),
                "gt_bfs_plain" if plain else "gt_bfs")
         return parent, level
 
@@ -299,8 +315,8 @@ def gt_bfs_batch(graphs, roots_per_graph, parents, levels, stream=None) -> None:
     counts = (ctypes.c_int32 * ng)(*[len(r) for r in roots_per_graph])
     flat = [int(x) for r in roots_per_graph for x in r]
     ra = (ctypes.c_int64 * max(1, len(flat)))(*flat)
-    pp = (ctypes.c_void_p * ng)(*[_ptr(x) for x in parents])
-    lp = (ctypes.c_void_p * ng)(*[_ptr(x) for x in levels])
+    pp = (ctypes.c_void_p * ng)(*[_out(x, len(r) * g.n, "parents") for x, r, g in zip(parents, roots_per_graph, graphs)])
+    lp = (ctypes.c_void_p * ng)(*[_out(x, len(r) * g.n, "levels") for x, r, g in zip(levels, roots_per_graph, graphs)])
     _check(lib().gt_bfs_batch(hs, ng, ra, counts, pp, lp, _stream(stream)), "gt_bfs_batch")
 
 
@@ -335,8 +351,9 @@ class Server:
 
     def submit(self, gid: int, root: int, parent, level) -> int:
         t = ctypes.c_uint64(0)
-        _check(lib().gt_serve_submit(self._h, int(gid), int(root), _ptr(parent), _ptr(level), ctypes.byref(t)),
-               "gt_serve_submit")
+        n = self._graphs[gid].n if 0 <= gid < len(self._graphs) else 0
+        _check(lib().gt_serve_submit(self._h, int(gid), int(root), _out(parent, n, "parent"), _out(level, n, "level"),
+                                     ctypes.byref(t)), "gt_serve_submit")
         return t.value
 
     def poll(self, ticket: int, timeout_ms: int = 10000) -> int:
@@ -369,8 +386,8 @@ class Server:
 def gt_bfs_csr_noalloc(row, col, n: int, root: int, parent, level, stream=None) -> None:
     """Plain BFS on a caller's device CSR without any device allocation (fixed scratch;
     n <= 262,144); same results as gt_bfs_plain."""
-    _check(lib().gt_bfs_csr_noalloc(_ptr(row), _ptr(col), int(n), int(root), _ptr(parent), _ptr(level),
-                                    _stream(stream)), "gt_bfs_csr_noalloc")
+    _check(lib().gt_bfs_csr_noalloc(_ptr(row), _ptr(col), int(n), int(root), _out(parent, n, "parent"),
+                                    _out(level, n, "level"), _stream(stream)), "gt_bfs_csr_noalloc")
 
 
 def gt_count_traversed(edges, level, stream=None, m: int | None = None) -> int:

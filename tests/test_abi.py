@@ -74,3 +74,13 @@ def test_defaults_and_errors_without_gpu():
 def test_no_cpu_fallback_in_binding():
     src = open(os.path.join(ROOT, "paper_2009_07463_gb300", "__init__.py")).read()
     assert "import oracle" not in src and "from oracle" not in src
+
+
+def test_binding_checks_output_buffers():
+    import numpy as np
+    ok = np.zeros(10, dtype=np.int32)
+    assert gt._out(ok, 10, "x") == ok.ctypes.data
+    for bad in (np.zeros(9, dtype=np.int32), np.zeros(10, dtype=np.int64), np.zeros(20, dtype=np.int32)[::2]):
+        with pytest.raises(ValueError):
+            gt._out(bad, 10, "x")
+    assert gt._out(None, 10, "x") == 0 and gt._out(1234, 10, "x") == 1234
