@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--study-roots", type=int, default=32)
     ap.add_argument("--serve-rates", default="4000,16000,48000")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-join-levels", type=int, default=-1,
+                    help="level boundaries at which queries may join a running batched launch (-1: library default)")
     ap.add_argument("--serve-policies", default="adaptive,batched,single",
                     help="server dispatch policies to run on each arrival schedule (the first is the headline)")
     return ap.parse_args()
@@ -620,10 +622,11 @@ def run_batch_workload(a, rank, local):
     print(json.dumps(out), flush=True)
 
 
-def _serve_once(gt, graphs, bufs, RING, nq, gaps, gsel, roots, policy):
+def _serve_once(gt, graphs, bufs, RING, nq, gaps, gsel, roots, policy, join_levels=-1):
     """One arrival schedule through a server with the given dispatch policy."""
     import threading
-    srv = gt.Server(hbm_budget_bytes=48 << 30, streams=2, max_batch_roots=128, window_us=100, policy=policy)
+    srv = gt.Server(hbm_budget_bytes=48 << 30, streams=2, max_batch_roots=128, window_us=100, policy=policy,
+                    join_levels=None if join_levels < 0 else join_levels)
     gids = [srv.add_graph(g) for g in graphs]
     slot_busy = [[None] * RING for _ in graphs]
     ring_pos = [0] * len(graphs)
@@ -663,7 +666,7 @@ def _serve_once(gt, graphs, bufs, RING, nq, gaps, gsel, roots, policy):
     srv.destroy()
     col.join()
     return {"qps": round(st["qps"], 1), "p50_us": round(st["p50_us"], 1), "p99_us": round(st["p99_us"], 1),
-            "batched_launches": st["batches"]}
+            "batched_launches": st["batches"], "joined": st["joined"]}
 
 
 def run_serve_workload(a, rank, local):
@@ -705,7 +708,7 @@ def run_serve_workload(a, rank, local):
         for pol in [x for x in a.serve_policies.split(",") if x]:
             served[pol] = _serve_once(gt, graphs, bufs, RING, nq, gaps, gsel, roots,
                                       {"adaptive": gt.GT_SERVE_ADAPTIVE, "batched": gt.GT_SERVE_BATCHED,
-                                       "single": gt.GT_SERVE_SINGLE}[pol])
+                                       "single": gt.GT_SERVE_SINGLE}[pol], a.serve_join_levels)
         # sequential single-root calls on the same schedule (one worker, FIFO)
         lat2 = []
         stream = torch.cuda.current_stream()

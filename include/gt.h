@@ -183,8 +183,10 @@ GT_API int gt_count_traversed(const int64_t* edges, int64_t m, const int32_t* le
  * single-root traversals back to back (one such flight per graph at a time), or one
  * batched launch (64 roots per lane word, as gt_bfs_batch) whose cost hardly depends on
  * how many lanes are filled. A batched launch goes at once when the GPU is idle,
- * otherwise after up to window_us to fill lane words (only where batching pays). Flights
- * on different streams overlap on the device. Each result equals gt_bfs from that root.
+ * otherwise after up to window_us to fill lane words (only where batching pays); queries
+ * that arrive while a batched launch of their graph runs join its free lanes at one of its
+ * first level boundaries (join_levels). Flights on different streams overlap on the
+ * device. Each result equals gt_bfs from that root.
  * While a graph is added to a running server, the caller must not traverse it through
  * gt_bfs, gt_bfs_plain, gt_bfs_trace or gt_autotune: those share its traversal state. */
 typedef struct gt_serve_config {
@@ -193,6 +195,9 @@ typedef struct gt_serve_config {
   int32_t max_batch_roots;  /* roots per launch (default 256) */
   double window_us;         /* wait to fill lane words while other batches run (default 200) */
   int32_t policy;           /* GT_SERVE_ADAPTIVE (default), GT_SERVE_BATCHED or GT_SERVE_SINGLE */
+  int32_t join_levels;      /* a batched launch takes newly submitted roots of its graph into
+                               free lanes at its first join_levels level boundaries (default 0:
+                               roots join only new launches) */
 } gt_serve_config;
 
 enum { GT_SERVE_ADAPTIVE = 0, GT_SERVE_BATCHED = 1, GT_SERVE_SINGLE = 2 };
@@ -202,6 +207,7 @@ typedef struct gt_serve_stats {
   double p50_us, p99_us, mean_us, max_us; /* submit -> results in the caller's buffers */
   double qps;                             /* completed / (last completion - first submit) */
   int64_t device_bytes;                   /* graphs + batch storage held against the budget */
+  int64_t joined;                         /* queries admitted into a running batched launch */
 } gt_serve_stats;
 
 typedef struct gt_server* gt_server_t;

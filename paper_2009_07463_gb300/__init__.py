@@ -44,13 +44,13 @@ class gt_level_info(ctypes.Structure):
 
 class gt_serve_config(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("streams", ctypes.c_int32), ("max_batch_roots", ctypes.c_int32),
-                ("window_us", ctypes.c_double), ("policy", ctypes.c_int32)]
+                ("window_us", ctypes.c_double), ("policy", ctypes.c_int32), ("join_levels", ctypes.c_int32)]
 
 
 class gt_serve_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "failed", "batches", "inflight", "pending")] + \
                [(n, ctypes.c_double) for n in ("p50_us", "p99_us", "mean_us", "max_us", "qps")] + \
-               [("device_bytes", ctypes.c_int64)]
+               [("device_bytes", ctypes.c_int64), ("joined", ctypes.c_int64)]
 
 
 class GtError(RuntimeError):
@@ -325,7 +325,7 @@ class Server:
 
     def __init__(self, hbm_budget_bytes: int | None = None, streams: int | None = None,
                  max_batch_roots: int | None = None, window_us: float | None = None,
-                 policy: int | None = None):
+                 policy: int | None = None, join_levels: int | None = None):
         cfg = gt_serve_config()
         lib().gt_serve_config_default(ctypes.byref(cfg))
         if hbm_budget_bytes is not None:
@@ -338,6 +338,8 @@ class Server:
             cfg.window_us = float(window_us)
         if policy is not None:
             cfg.policy = int(policy)
+        if join_levels is not None:
+            cfg.join_levels = int(join_levels)
         h = ctypes.c_void_p()
         _check(lib().gt_serve_create(ctypes.byref(cfg), ctypes.byref(h)), "gt_serve_create")
         self._h = h.value

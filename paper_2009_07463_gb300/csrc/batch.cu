@@ -73,7 +73,8 @@ struct SlotDev {
   int32_t* outl[64];
   int32_t nlanes;
   int32_t alpha, beta;
-  int32_t pad;
+  int32_t join_max;      // last level boundary at which mailbox roots may join (0: none)
+  BatchMailbox* mb;      // mapped mailbox shared by the launch's slots (null: none)
   uint64_t active;
   LaneInit lane[64];
 };
@@ -305,6 +306,62 @@ __global__ void batch_init(SlotDev* slots, SlotCtl* sctl, int nslots) {
   }
 }
 
+__device__ void lane_walk(const SlotDev& s, LaneInit& li);
+
+// Level boundary of a launch with a mailbox (one thread): published roots move into free
+// lanes of the launch's slots, in slot order. A lane joining a slot at its boundary J
+// (the slot's next iteration) starts at its core vertex on iteration J, so its levels are
+// iteration - J + hops; the start vertex enters the slot's next frontier. Sets `closed`
+// once no slot can take a root at a later boundary.
+__device__ void admit_roots(SlotDev* slots, SlotCtl* sctl, int nslots, const int* s_done, const int* s_cur,
+                            const int* s_it) {
+  BatchMailbox* mb = slots[0].mb;
+  if (!mb) return;
+  volatile BatchMailbox* vm = mb;
+  if (vm->closed) return;
+  const int join_max = slots[0].join_max;
+  int taken = vm->taken;
+  const int count = min(vm->count, MAILBOX_CAP);
+  __threadfence_system();  // the entries below were published before this count
+  bool later = false;
+  for (int si = 0; si < nslots; ++si) {
+    if (s_done[si]) continue;
+    const int J = s_it[si] + 1;
+    if (J > join_max) continue;
+    SlotDev& s = slots[si];
+    SlotCtl& c = sctl[si];
+    const int nxt = s_cur[si] ^ 1;
+    while (taken < count && s.nlanes < 64) {
+      const int l = s.nlanes;
+      LaneInit& li = s.lane[l];
+      li.root = (int32_t)vm->e[taken].root;
+      s.outp[l] = vm->e[taken].outp;
+      s.outl[l] = vm->e[taken].outl;
+      lane_walk(s, li);
+      li.base -= J;
+      if (li.start >= 0) {
+        const uint64_t bit = 1ull << l;
+        s.visit[li.start] |= bit;
+        s.P[(int64_t)li.start * 64 + l] = li.sparent;
+        s.L[(int64_t)li.start * 64 + l] = (uint16_t)J;
+        const uint64_t old = s.front[nxt][li.start];
+        s.front[nxt][li.start] = old | bit;
+        if (old == 0) {
+          s.fl[nxt][c.fl_n[nxt]++] = li.start;
+          c.m_next += s.crow[li.start + 1] - s.crow[li.start];
+        }
+        s.active |= bit;
+      }
+      s.nlanes = l + 1;
+      ++taken;
+    }
+    if (J < join_max && s.nlanes < 64) later = true;
+  }
+  vm->taken = taken;
+  if (!later) vm->closed = 1;
+  __threadfence_system();
+}
+
 __global__ void __launch_bounds__(BT) batch_run(SlotDev* slots, SlotCtl* sctl, int nslots, BatchCtl* bc) {
   __shared__ int s_cur[MAX_SLOTS_SMEM], s_dir[MAX_SLOTS_SMEM], s_done[MAX_SLOTS_SMEM], s_it[MAX_SLOTS_SMEM];
   __shared__ int64_t s_ncur[MAX_SLOTS_SMEM];
@@ -347,7 +404,7 @@ __global__ void __launch_bounds__(BT) batch_run(SlotDev* slots, SlotCtl* sctl, i
         // pull: every core vertex still missing lanes scans its ascending adjacency for the
         // first neighbour carrying each missing lane (min-id parents). Short adjacencies:
         // a lane each; long ones: chunks, a warp each, parents by atomicMin.
-        const uint64_t act = s.active;
+        const uint64_t act = *(volatile const uint64_t*)&s.active;  // lanes may have joined at the last boundary
         for (int64_t i0 = gw * 32; i0 < s.n_lanes; i0 += nw * 32) {
           const int64_t i = i0 + lane;
           int32_t w = -1;
@@ -432,6 +489,8 @@ __global__ void __launch_bounds__(BT) batch_run(SlotDev* slots, SlotCtl* sctl, i
       for (int64_t j = gtid(); j < nf; j += gthreads()) s.front[cur][s.fl[cur][j]] = 0;
     }
     if (blockIdx.x == 0) {
+      if (threadIdx.x == 0 && slots[0].mb) admit_roots(slots, sctl, nslots, s_done, s_cur, s_it);
+      __syncthreads();
       for (int si = threadIdx.x; si < nslots; si += BT) {
         if (s_done[si]) continue;
         SlotCtl& c = sctl[si];
@@ -576,7 +635,35 @@ __global__ void batch_resolve(SlotDev* slots, const ResolveSeg* segs, int nslots
   }
 }
 
-// Lane setup on the device: the Alg. 9 walk of every root (one thread per lane).
+// The Alg. 9 walk of a lane's root to its core vertex: start (core id, -1: nothing to
+// traverse), base (hops), sparent (the start vertex's parent).
+__device__ void lane_walk(const SlotDev& s, LaneInit& li) {
+  const int32_t root = li.root;
+  const int32_t info = s.vinfo[root];
+  if (info >= 0) {
+    li.start = info;
+    li.base = 0;
+    li.sparent = root;
+    return;
+  }
+  int32_t v = root, hops = 0, start = -1;
+  for (int64_t guard = 0; guard < s.n; ++guard) {
+    const int32_t u = s.up[v];
+    if (u < 0) break;
+    ++hops;
+    const int32_t cu = s.old2core[u];
+    if (cu >= 0) {
+      start = cu;
+      break;
+    }
+    v = u;
+  }
+  li.start = start;
+  li.base = hops;
+  li.sparent = v;
+}
+
+// Lane setup on the device (one thread per lane).
 __global__ void batch_lanes(SlotDev* slots, int nslots) {
   const int si = blockIdx.x;
   if (si >= nslots) return;
@@ -584,29 +671,7 @@ __global__ void batch_lanes(SlotDev* slots, int nslots) {
   const int l = threadIdx.x;
   if (l >= s.nlanes) return;
   LaneInit& li = s.lane[l];
-  const int32_t root = li.root;
-  const int32_t info = s.vinfo[root];
-  if (info >= 0) {
-    li.start = info;
-    li.base = 0;
-    li.sparent = root;
-  } else {
-    int32_t v = root, hops = 0, start = -1;
-    for (int64_t guard = 0; guard < s.n; ++guard) {
-      const int32_t u = s.up[v];
-      if (u < 0) break;
-      ++hops;
-      const int32_t cu = s.old2core[u];
-      if (cu >= 0) {
-        start = cu;
-        break;
-      }
-      v = u;
-    }
-    li.start = start;
-    li.base = hops;
-    li.sparent = v;
-  }
+  lane_walk(s, li);
   const unsigned long long bit = li.start >= 0 ? (1ull << l) : 0ull;
   if (bit) atomicOr((unsigned long long*)&s.active, bit);
 }
@@ -683,7 +748,8 @@ void enqueue_batch(SlotDev* d_slots, SlotCtl* d_ctl, BatchCtl* d_bc, ResolveSeg*
 
 }  // namespace
 
-int batch_launch(BatchCtx* ctx, const SlotSpec* specs, int nspecs, int sm_share, cudaStream_t st) {
+int batch_launch(BatchCtx* ctx, const SlotSpec* specs, int nspecs, int sm_share, cudaStream_t st, BatchMailbox* mb,
+                 int join_max) {
   if (nspecs <= 0) return GT_OK;
   if (nspecs > MAX_SLOTS_SMEM) {
     set_error("batched BFS: more than 256 lane words (16384 roots) in one launch");
@@ -752,6 +818,8 @@ int batch_launch(BatchCtx* ctx, const SlotSpec* specs, int nspecs, int sm_share,
     d.nlanes = sp.nlanes;
     d.alpha = g->tuning.batch_alpha;
     d.beta = g->tuning.batch_beta;
+    d.mb = mb;
+    d.join_max = mb ? join_max : 0;
     for (int l = 0; l < sp.nlanes; ++l) {
       const int64_t root = sp.roots[l];
       if (root < 0 || root >= g->n || !sp.outp[l] || !sp.outl[l]) {

@@ -186,6 +186,24 @@ struct SlotSpec {
   int32_t* const* outp;     // nlanes parent arrays (device, n entries)
   int32_t* const* outl;     // nlanes level arrays
 };
+
+// Roots that join a running batched launch at a level boundary (serving). The host
+// publishes entries and then raises `count`; at each level boundary up to `join_max` the
+// launch moves published entries into free lanes of the slots that share the mailbox,
+// raises `taken`, and sets `closed` once it will take no more. Lives in page-locked host
+// memory mapped into the device.
+constexpr int MAILBOX_CAP = 256;
+struct BatchMailbox {
+  int32_t count;   // host: entries published
+  int32_t taken;   // device: entries admitted into lanes
+  int32_t closed;  // device: 1 when no more entries will be admitted
+  int32_t pad;
+  struct Entry {
+    int64_t root;
+    int32_t* outp;  // device int32[n]
+    int32_t* outl;
+  } e[MAILBOX_CAP];
+};
 int run_batch(gt_graph* const* graphs, int ngraphs, const int64_t* roots, const int32_t* roots_per_graph,
               int32_t* const* parent, int32_t* const* level, cudaStream_t s);
 int ensure_slots(gt_graph* g, int need);
@@ -196,7 +214,10 @@ void slot_sizes(const gt_graph* g, size_t sz[SLOT_BUFS]);
 size_t slot_bytes(const gt_graph* g);
 // Enqueues a whole batched traversal on `st` (cooperative kernel on sm_share SMs' worth of
 // CTAs, 0 = all); batch_status() reads its outcome once the stream has passed it.
-int batch_launch(BatchCtx* ctx, const SlotSpec* specs, int nspecs, int sm_share, cudaStream_t st);
+// mb (device address of a mapped mailbox, or null): roots may join the launch mid-flight,
+// up to level boundary join_max.
+int batch_launch(BatchCtx* ctx, const SlotSpec* specs, int nspecs, int sm_share, cudaStream_t st,
+                 BatchMailbox* mb = nullptr, int join_max = 0);
 int batch_status(const BatchCtx* ctx);
 void batch_ctx_free(BatchCtx* c);
 void free_batch_mem(gt_graph* g);

@@ -17,6 +17,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -80,6 +81,9 @@ struct Flight {
   std::vector<Query*> queries;
   std::vector<int> slots;
   std::vector<QueryDone> done;
+  BatchMailbox* mb = nullptr;  // batched: roots joining while it runs (host address)
+  int capacity = 0;            // free lanes the launch can still fill
+  std::vector<Query*> late;    // queries published in mb, in mailbox order
 };
 
 double ema(double old, double x) { return old > 0 ? 0.8 * old + 0.2 * x : x; }
@@ -101,9 +105,10 @@ struct gt_server {
   std::vector<cudaStream_t> streams;
   std::vector<gt::BatchCtx> ctxs;
   std::vector<gt::Flight*> flights;  // per stream, null when free
+  std::vector<gt::BatchMailbox*> mbox, mbox_dev;  // per stream: pinned mailbox (host / device address)
   int64_t used_bytes = 0;
   // statistics
-  int64_t submitted = 0, completed = 0, failed = 0, batches = 0;
+  int64_t submitted = 0, completed = 0, failed = 0, batches = 0, joined = 0;
   double t_first = 0, t_last = 0;
   std::vector<double> lat_us;
 };
@@ -146,6 +151,15 @@ void CUDART_CB on_flight_done(void* arg) {
   GraphEntry& ge = s->graphs[f->gid];
   if (!f->slots.empty()) ge.est_word_us = ema(ge.est_word_us, (t - f->t_launch) / f->slots.size());
   for (int k : f->slots) ge.free_slots.push_back(k);
+  // the launch has finished: the mailbox counts are final
+  size_t taken = 0;
+  if (f->mb) {
+    const int32_t tk = ((volatile BatchMailbox*)f->mb)->taken;
+    taken = (size_t)std::max<int32_t>(0, std::min<int32_t>(tk, (int32_t)f->late.size()));
+  }
+  for (size_t i = 0; i < taken; ++i) f->queries.push_back(f->late[i]);
+  for (size_t i = f->late.size(); i > taken; --i) ge.pending.push_front(f->late[i - 1]);  // not admitted: back in line
+  s->joined += (int64_t)taken;
   for (Query* q : f->queries) {
     q->done = true;
     q->rc = rc;
@@ -207,6 +221,24 @@ void scheduler(gt_server* s) {
       else if (free_stream < 0) free_stream = (int)i;
     }
     if (s->stop && busy == 0) break;
+    // pending roots of a graph with a batched launch in flight join its free lanes
+    for (Flight* f : s->flights) {
+      if (!f || f->single || !f->mb || s->stop) continue;
+      volatile BatchMailbox* vm = f->mb;
+      if (vm->closed) continue;
+      GraphEntry& ge = s->graphs[f->gid];
+      while (!ge.pending.empty() && (int)f->late.size() < f->capacity) {
+        Query* q = ge.pending.front();
+        ge.pending.pop_front();
+        const int k = (int)f->late.size();
+        vm->e[k].root = q->root;
+        vm->e[k].outp = q->parent;
+        vm->e[k].outl = q->level;
+        std::atomic_thread_fence(std::memory_order_release);  // entry before count
+        vm->count = k + 1;
+        f->late.push_back(q);
+      }
+    }
     const int gi = oldest_graph(s);
     if (s->stop || gi < 0 || free_stream < 0) {
       s->cv_sched.wait_for(lk, std::chrono::microseconds(200));
@@ -334,8 +366,19 @@ void scheduler(gt_server* s) {
     cudaStream_t st = s->streams[free_stream];
     BatchCtx* ctx = &s->ctxs[free_stream];
     const int share = std::max(1, s->sms / (int)s->streams.size());
+    f->capacity = s->cfg.join_levels > 0 ? std::min<int>(MAILBOX_CAP, words * 64 - (int)take) : 0;
+    BatchMailbox* mb_dev = nullptr;
+    if (f->capacity > 0) {
+      f->mb = s->mbox[free_stream];
+      volatile BatchMailbox* vm = f->mb;
+      vm->count = 0;
+      vm->taken = 0;
+      vm->closed = 0;
+      std::atomic_thread_fence(std::memory_order_release);
+      mb_dev = s->mbox_dev[free_stream];
+    }
     lk.unlock();
-    int rc = batch_launch(ctx, specs.data(), words, share, st);
+    int rc = batch_launch(ctx, specs.data(), words, share, st, mb_dev, s->cfg.join_levels);
     if (rc == GT_OK) rc = cuda_fail(cudaLaunchHostFunc(st, on_flight_done, f), "host callback");
     lk.lock();
     if (rc != GT_OK) {  // nothing will call back: fail the queries here
@@ -350,6 +393,16 @@ void scheduler(gt_server* s) {
       s->cv_done.notify_all();
     }
   }
+  // queries a last launch did not admit came back to the queues: they fail like the rest
+  for (GraphEntry& ge : s->graphs)
+    while (!ge.pending.empty()) {
+      Query* q = ge.pending.front();
+      ge.pending.pop_front();
+      q->done = true;
+      q->rc = GT_EBUSY;
+      s->failed++;
+    }
+  s->cv_done.notify_all();
 }
 
 }  // namespace
@@ -367,6 +420,7 @@ GT_API void gt_serve_config_default(gt_serve_config* c) {
   c->max_batch_roots = 256;
   c->window_us = 200.0;
   c->policy = GT_SERVE_ADAPTIVE;
+  c->join_levels = 0;  // measured: joins lengthen launches more than they save waiting
 }
 
 GT_API int gt_serve_create(const gt_serve_config* cfg, gt_server_t* out) {
@@ -380,7 +434,7 @@ GT_API int gt_serve_create(const gt_serve_config* cfg, gt_server_t* out) {
     gt_serve_config_default(&s->cfg);
   if (s->cfg.streams < 1 || s->cfg.streams > 16 || s->cfg.max_batch_roots < 1 || s->cfg.max_batch_roots > 16384 ||
       s->cfg.hbm_budget_bytes < 0 || s->cfg.window_us < 0 || s->cfg.policy < GT_SERVE_ADAPTIVE ||
-      s->cfg.policy > GT_SERVE_SINGLE) {
+      s->cfg.policy > GT_SERVE_SINGLE || s->cfg.join_levels < 0 || s->cfg.join_levels > 64) {
     delete s;
     set_error("gt_serve_create: configuration out of range");
     return GT_EINVAL;
@@ -390,11 +444,32 @@ GT_API int gt_serve_create(const gt_serve_config* cfg, gt_server_t* out) {
   s->streams.resize(s->cfg.streams);
   s->ctxs.resize(s->cfg.streams);
   s->flights.assign(s->cfg.streams, nullptr);
+  s->mbox.assign(s->cfg.streams, nullptr);
+  s->mbox_dev.assign(s->cfg.streams, nullptr);
+  for (int i = 0; i < s->cfg.streams; ++i) {
+    void* h = nullptr;
+    void* d = nullptr;
+    if (cudaHostAlloc(&h, sizeof(BatchMailbox), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer(&d, h, 0) != cudaSuccess) {
+      cudaGetLastError();
+      if (h) cudaFreeHost(h);
+      for (auto* m : s->mbox)
+        if (m) cudaFreeHost(m);
+      delete s;
+      set_error("gt_serve_create: pinned mailbox allocation failed");
+      return GT_ENOMEM;
+    }
+    memset(h, 0, sizeof(BatchMailbox));
+    s->mbox[i] = (BatchMailbox*)h;
+    s->mbox_dev[i] = (BatchMailbox*)d;
+  }
   for (auto& st : s->streams) {
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
       cudaGetLastError();
       for (auto& t : s->streams)
         if (t) cudaStreamDestroy(t);
+      for (auto* m : s->mbox)
+        if (m) cudaFreeHost(m);
       delete s;
       set_error("gt_serve_create: stream creation failed");
       return GT_EDEVICE;
@@ -491,6 +566,7 @@ GT_API int gt_serve_get_stats(gt_server_t s, gt_serve_stats* out) {
   out->completed = s->completed;
   out->failed = s->failed;
   out->batches = s->batches;
+  out->joined = s->joined;
   for (auto* f : s->flights) out->inflight += f ? 1 : 0;
   for (auto& ge : s->graphs) out->pending += (int64_t)ge.pending.size();
   out->device_bytes = s->used_bytes;
@@ -514,7 +590,7 @@ GT_API int gt_serve_reset_stats(gt_server_t s) {
   if (!s) return GT_EINVAL;
   std::lock_guard<std::mutex> lk(s->mu);
   s->lat_us.clear();
-  s->submitted = s->completed = s->failed = s->batches = 0;
+  s->submitted = s->completed = s->failed = s->batches = s->joined = 0;
   s->t_first = s->t_last = 0;
   return GT_OK;
 }
@@ -535,6 +611,8 @@ GT_API int gt_serve_destroy(gt_server_t s) {
       ge.g->last_stream = nullptr;
   for (auto st : s->streams) cudaStreamDestroy(st);
   for (auto& c : s->ctxs) batch_ctx_free(&c);
+  for (auto* m : s->mbox)
+    if (m) cudaFreeHost(m);
   for (auto& ge : s->graphs)
     for (auto& b : ge.slots)
       for (int i = 0; i < SLOT_BUFS; ++i) cudaFree(b.p[i]);

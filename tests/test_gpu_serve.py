@@ -126,3 +126,31 @@ def test_destroy_with_queries_outstanding(torch, graphs):
     for k in range(50):
         srv.submit(gid, k, *bufs[k])
     srv.destroy()  # finishes what is in flight, fails the rest, returns
+
+
+def test_roots_join_a_running_launch(torch):
+    # one root starts a batched launch; more roots of the same graph arrive while it runs
+    # and join its free lanes at a level boundary; every result equals gt_bfs alone
+    n = 1 << 18
+    e = graphgen.rmat_edges(18, 16, seed=91)
+    g = gt.gt_graph_build(e, n)
+    cand = graphgen.pick_roots(92, n, 64, g.degree()).tolist()
+    joined = 0
+    for attempt in range(3):
+        srv = gt.Server(streams=1, max_batch_roots=64, policy=gt.GT_SERVE_BATCHED, join_levels=4)
+        gid = srv.add_graph(g)
+        bufs = [(torch.empty(n, dtype=torch.int32, device="cuda"), torch.empty(n, dtype=torch.int32, device="cuda"))
+                for _ in cand]
+        tickets = [srv.submit(gid, cand[0], *bufs[0])]
+        time.sleep(0.0002)
+        tickets += [srv.submit(gid, r, *b) for r, b in zip(cand[1:], bufs[1:])]
+        for t in tickets:
+            assert srv.poll(t, 30000) == gt.GT_OK
+        joined = srv.stats()["joined"]
+        for r, (p, l) in zip(cand, bufs):
+            pa, la = g.bfs(r)
+            assert np.array_equal(l.cpu().numpy(), la) and np.array_equal(p.cpu().numpy(), pa), f"root {r}"
+        srv.destroy()
+        if joined > 0:
+            break
+    assert joined > 0, "no root joined a running launch in three tries"
