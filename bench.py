@@ -666,7 +666,7 @@ def _serve_once(gt, graphs, bufs, RING, nq, gaps, gsel, roots, policy, join_leve
     srv.destroy()
     col.join()
     return {"qps": round(st["qps"], 1), "p50_us": round(st["p50_us"], 1), "p99_us": round(st["p99_us"], 1),
-            "batched_launches": st["batches"], "joined": st["joined"]}
+            "batched_launches": st["batches"], "joined": st["joined"], "early": st["early"]}
 
 
 def run_serve_workload(a, rank, local):

@@ -185,8 +185,10 @@ GT_API int gt_count_traversed(const int64_t* edges, int64_t m, const int32_t* le
  * how many lanes are filled. A batched launch goes at once when the GPU is idle,
  * otherwise after up to window_us to fill lane words (only where batching pays); queries
  * that arrive while a batched launch of their graph runs join its free lanes at one of its
- * first level boundaries (join_levels). Flights on different streams overlap on the
- * device. Each result equals gt_bfs from that root.
+ * first level boundaries (join_levels); in a lane word that took joined roots, each lane's
+ * results are written, and its query completes, when that lane's traversal ends, even
+ * while the launch goes on. Flights on different streams overlap on the device. Each
+ * result equals gt_bfs from that root.
  * While a graph is added to a running server, the caller must not traverse it through
  * gt_bfs, gt_bfs_plain, gt_bfs_trace or gt_autotune: those share its traversal state. */
 typedef struct gt_serve_config {
@@ -208,6 +210,7 @@ typedef struct gt_serve_stats {
   double qps;                             /* completed / (last completion - first submit) */
   int64_t device_bytes;                   /* graphs + batch storage held against the budget */
   int64_t joined;                         /* queries admitted into a running batched launch */
+  int64_t early;                          /* queries completed before their batched launch ended */
 } gt_serve_stats;
 
 typedef struct gt_server* gt_server_t;

@@ -50,7 +50,7 @@ class gt_serve_config(ctypes.Structure):
 class gt_serve_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "failed", "batches", "inflight", "pending")] + \
                [(n, ctypes.c_double) for n in ("p50_us", "p99_us", "mean_us", "max_us", "qps")] + \
-               [("device_bytes", ctypes.c_int64), ("joined", ctypes.c_int64)]
+               [("device_bytes", ctypes.c_int64), ("joined", ctypes.c_int64), ("early", ctypes.c_int64)]
 
 
 class GtError(RuntimeError):

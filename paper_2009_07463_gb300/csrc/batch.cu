@@ -74,7 +74,10 @@ struct SlotDev {
   int32_t nlanes;
   int32_t alpha, beta;
   int32_t join_max;      // last level boundary at which mailbox roots may join (0: none)
-  BatchMailbox* mb;      // mapped mailbox shared by the launch's slots (null: none)
+  BatchMailbox* mb;      // mapped mailbox shared by the launch's slots (null: none; with one,
+                         // lanes that finish early are written and reported at once)
+  uint64_t emitted;      // lanes whose results are already written
+  uint64_t joined;       // lanes admitted from the mailbox during the launch
   uint64_t active;
   LaneInit lane[64];
 };
@@ -84,13 +87,24 @@ struct SlotCtl {
   int64_t m_next;  // summed degree of the next frontier
   int64_t q_n;     // top-down chunk queue entries
   int32_t cur, dir, done, iter;
+  uint64_t alive;  // lanes present in the next frontier (early completion)
+  uint64_t fin;    // lanes whose results are written at this level boundary
 };
+
+struct ResolveSeg {
+  const int32_t* list;
+  const int32_t* lup;
+  int64_t b, e;
+};
+
+// Bits of lanes 0 .. nlanes-1.
+__device__ __forceinline__ uint64_t lanes_of(int nlanes) { return nlanes >= 64 ? ~0ull : (1ull << nlanes) - 1; }
 
 struct BatchCtl {
   unsigned int bar;  // grid barrier arrivals
   int err;
   int live;          // slots not done
-  int pad;
+  int emit;          // slots with lanes to write at this level boundary
 };
 
 // Grid-wide barrier for a cooperative launch: arrivals counted on one word, each CTA
@@ -307,6 +321,12 @@ __global__ void batch_init(SlotDev* slots, SlotCtl* sctl, int nslots) {
 }
 
 __device__ void lane_walk(const SlotDev& s, LaneInit& li);
+template <bool HOIST>
+__device__ void write_lanes(const SlotDev& s, uint64_t mask);
+__device__ void fixup_lane(const SlotDev& s, int l);
+__device__ void resolve_lanes(const SlotDev& s, const ResolveSeg& sg, const int8_t* ls, int nl, int64_t t0,
+                              int64_t nt);
+__device__ int list_lanes(uint64_t mask, int8_t* ls);
 
 // Level boundary of a launch with a mailbox (one thread): published roots move into free
 // lanes of the launch's slots, in slot order. A lane joining a slot at its boundary J
@@ -337,6 +357,7 @@ __device__ void admit_roots(SlotDev* slots, SlotCtl* sctl, int nslots, const int
       li.root = (int32_t)vm->e[taken].root;
       s.outp[l] = vm->e[taken].outp;
       s.outl[l] = vm->e[taken].outl;
+      vm->e[taken].lane_id = si * 64 + l;
       lane_walk(s, li);
       li.base -= J;
       if (li.start >= 0) {
@@ -351,20 +372,68 @@ __device__ void admit_roots(SlotDev* slots, SlotCtl* sctl, int nslots, const int
           c.m_next += s.crow[li.start + 1] - s.crow[li.start];
         }
         s.active |= bit;
+        s.joined |= bit;
+        c.alive |= bit;
       }
       s.nlanes = l + 1;
       ++taken;
     }
     if (J < join_max && s.nlanes < 64) later = true;
   }
+  __threadfence_system();  // lane ids of the admitted entries before the new count
   vm->taken = taken;
   if (!later) vm->closed = 1;
   __threadfence_system();
 }
 
-__global__ void __launch_bounds__(BT) batch_run(SlotDev* slots, SlotCtl* sctl, int nslots, BatchCtl* bc) {
+// With a mailbox (roots may join a running launch, so lanes can end many levels apart),
+// lanes whose traversal has ended (no discovery at a level) while their slot goes on are
+// written out at that level boundary: outputs, root walk and resolution for those lanes
+// only, grid barriers between the steps; then their bits are set in the mailbox's done
+// words for the host. They also leave the bottom-up miss masks. Not inlined: the
+// traversal loop keeps its own register budget.
+__device__ __noinline__ bool emit_lanes(SlotDev* slots, SlotCtl* sctl, int nslots, BatchCtl* bc,
+                                        const ResolveSeg* segs, int maxh, unsigned int& gen) {
+  __shared__ int8_t ls[64];
+  __shared__ int nl;
+  for (int si = 0; si < nslots; ++si) {
+    const uint64_t fin = *(volatile const uint64_t*)&sctl[si].fin;
+    if (fin) write_lanes<false>(slots[si], fin);
+  }
+  if (!grid_barrier(bc, gen)) return false;
+  for (int64_t t = gtid(); t < (int64_t)nslots * 64; t += gthreads()) {
+    const int si = (int)(t >> 6), l = (int)(t & 63);
+    if ((*(volatile const uint64_t*)&sctl[si].fin >> l) & 1ull) fixup_lane(slots[si], l);
+  }
+  for (int h = 0; h < maxh; ++h) {
+    if (!grid_barrier(bc, gen)) return false;
+    for (int si = 0; si < nslots; ++si) {
+      const uint64_t fin = *(volatile const uint64_t*)&sctl[si].fin;
+      if (!fin) continue;
+      __syncthreads();
+      if (threadIdx.x == 0) nl = list_lanes(fin, ls);
+      __syncthreads();
+      resolve_lanes(slots[si], segs[(size_t)h * nslots + si], ls, nl, gtid(), gthreads());
+    }
+  }
+  __threadfence_system();  // results reach memory before the host sees the done bits
+  if (!grid_barrier(bc, gen)) return false;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    volatile BatchMailbox* vm = slots[0].mb;
+    for (int si = 0; si < nslots && si < MAILBOX_WORDS; ++si) {
+      const uint64_t fin = *(volatile const uint64_t*)&sctl[si].fin;
+      if (fin) vm->done[si] = vm->done[si] | fin;
+    }
+    __threadfence_system();
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(BT)
+    batch_run(SlotDev* slots, SlotCtl* sctl, int nslots, BatchCtl* bc, const ResolveSeg* segs, int maxh) {
   __shared__ int s_cur[MAX_SLOTS_SMEM], s_dir[MAX_SLOTS_SMEM], s_done[MAX_SLOTS_SMEM], s_it[MAX_SLOTS_SMEM];
   __shared__ int64_t s_ncur[MAX_SLOTS_SMEM];
+  const bool early = slots[0].mb != nullptr;
   const int lane = threadIdx.x & 31;
   const int64_t gw = gtid() >> 5, nw = gthreads() >> 5;
   unsigned int gen = 0;
@@ -469,15 +538,23 @@ __global__ void __launch_bounds__(BT) batch_run(SlotDev* slots, SlotCtl* sctl, i
       const int64_t nn = sctl[si].fl_n[nxt];
       const uint16_t it = (uint16_t)(s_it[si] + 1);
       int64_t msum = 0;
+      uint64_t alive = 0;
       for (int64_t j = gtid(); j < nn; j += gthreads()) {
         const int32_t w = s.fl[nxt][j];
         const uint64_t nb = fn[w];
         msum += s.crow[w + 1] - s.crow[w];
         set_lane_levels(s, w, nb, it);
         s.visit[w] |= nb;
+        alive |= nb;
       }
       msum = warp_sum(msum);
       if (lane == 0 && msum) atomicAdd((unsigned long long*)&sctl[si].m_next, (unsigned long long)msum);
+      if (early) {
+        const uint32_t lo = __reduce_or_sync(0xffffffffu, (uint32_t)alive);
+        const uint32_t hi = __reduce_or_sync(0xffffffffu, (uint32_t)(alive >> 32));
+        alive = ((uint64_t)hi << 32) | lo;
+        if (lane == 0 && alive) atomicOr((unsigned long long*)&sctl[si].alive, (unsigned long long)alive);
+      }
     }
     if (!grid_barrier(bc, gen)) return;
     // ---- D: clear the old frontier words, then one thread per slot decides
@@ -489,12 +566,14 @@ __global__ void __launch_bounds__(BT) batch_run(SlotDev* slots, SlotCtl* sctl, i
       for (int64_t j = gtid(); j < nf; j += gthreads()) s.front[cur][s.fl[cur][j]] = 0;
     }
     if (blockIdx.x == 0) {
-      if (threadIdx.x == 0 && slots[0].mb) admit_roots(slots, sctl, nslots, s_done, s_cur, s_it);
+      if (threadIdx.x == 0) bc->emit = 0;
+      if (threadIdx.x == 0 && early) admit_roots(slots, sctl, nslots, s_done, s_cur, s_it);
       __syncthreads();
       for (int si = threadIdx.x; si < nslots; si += BT) {
-        if (s_done[si]) continue;
         SlotCtl& c = sctl[si];
-        const SlotDev& s = slots[si];
+        c.fin = 0;
+        if (s_done[si]) continue;
+        SlotDev& s = slots[si];
         const int cur = s_cur[si], nxt = cur ^ 1;
         const int64_t nn = c.fl_n[nxt];
         c.fl_n[cur] = 0;
@@ -511,80 +590,94 @@ __global__ void __launch_bounds__(BT) batch_run(SlotDev* slots, SlotCtl* sctl, i
           if (nn * (int64_t)s.beta < s.nc && nn < s_ncur[si]) c.dir = DIR_TD;
         }
         c.m_next = 0;
+        const uint64_t alive = c.alive;
+        c.alive = 0;
+        // lanes ending with their slot are left to the output kernels, and so are all of a
+        // slot without joined lanes: lanes started together end a few levels apart
+        if (early && !c.done && (s.joined & ~s.emitted)) {
+          const uint64_t fin = lanes_of(s.nlanes) & ~s.emitted & ~alive;
+          if (fin) {
+            c.fin = fin;
+            s.emitted |= fin;
+            s.active &= ~fin;
+            atomicAdd(&bc->emit, 1);
+          }
+        }
       }
     }
     if (!grid_barrier(bc, gen)) return;
+    if (early && *(volatile int*)&bc->emit && !emit_lanes(slots, sctl, nslots, bc, segs, maxh, gen)) return;
     if (*(volatile int*)&bc->live <= 0) return;
   }
 }
 
-// Root-major outputs in vertex-id order. A CTA takes 32 consecutive vertices; warp k
-// writes lanes 8k..8k+7 of the slot, each lane's 32 values coalesced. Core vertices and
-// tree vertices hanging from a core vertex are final here; tree vertices hanging from a
-// tree vertex get -2 ("resolve pending") for batch_resolve.
-__global__ void __launch_bounds__(BT) batch_output(SlotDev* slots, int nslots) {
+// Root-major outputs in vertex-id order for the lanes in `mask`. A CTA takes 32
+// consecutive vertices; warp k writes lanes 8k..8k+7 of the slot, each lane's 32 values
+// coalesced. Core vertices and tree vertices hanging from a core vertex are final here;
+// tree vertices hanging from a tree vertex get -2 ("resolve pending") for the resolution.
+// HOIST keeps the 8 lanes' output pointers in registers (the output kernel); without it
+// they are re-read per chunk (inside the traversal kernel, whose registers are tight).
+template <bool HOIST>
+__device__ void write_lanes(const SlotDev& s, uint64_t mask) {
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  for (int si = 0; si < nslots; ++si) {
-    const SlotDev& s = slots[si];
-    const int nl = min(8, s.nlanes - wp * 8);  // lanes of the slot this warp writes
-    if (nl <= 0) continue;
-    int32_t* op[8];
-    int32_t* ol[8];
-    int32_t base[8];
+  const uint32_t wm = (uint32_t)(mask >> (wp * 8)) & 0xFFu;  // lanes of the slot this warp writes
+  if (!wm) return;
+  int32_t* op[8];
+  int32_t* ol[8];
+  int32_t base[8];
+  if (HOIST) {
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      op[k] = k < nl ? s.outp[wp * 8 + k] : nullptr;
-      ol[k] = k < nl ? s.outl[wp * 8 + k] : nullptr;
-      base[k] = k < nl ? s.lane[wp * 8 + k].base : 0;
+      const bool on = (wm >> k) & 1u;
+      op[k] = on ? s.outp[wp * 8 + k] : nullptr;
+      ol[k] = on ? s.outl[wp * 8 + k] : nullptr;
+      base[k] = on ? s.lane[wp * 8 + k].base : 0;
     }
-    const int64_t nchunks = (s.n + 31) / 32;
-    for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
-      const int64_t v = c * 32 + lane;
-      const bool in = v < s.n;
-      const int32_t info = in ? s.vinfo[v] : -1;
-      int32_t cid = -1, add = 0, fixed_parent = -1;
-      if (info >= 0) {
-        cid = info;
-      } else if (info <= -2 && info != INT32_MIN) {
-        cid = s.anchor_cid[-2 - info];
-        add = 1;
-        fixed_parent = s.anchor_vid[-2 - info];
+  }
+  const int64_t nchunks = (s.n + 31) / 32;
+  for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const int64_t v = c * 32 + lane;
+    const bool in = v < s.n;
+    const int32_t info = in ? s.vinfo[v] : -1;
+    int32_t cid = -1, add = 0, fixed_parent = -1;
+    if (info >= 0) {
+      cid = info;
+    } else if (info <= -2 && info != INT32_MIN) {
+      cid = s.anchor_cid[-2 - info];
+      add = 1;
+      fixed_parent = s.anchor_vid[-2 - info];
+    }
+    const uint32_t vis = cid >= 0 ? (uint32_t)(s.visit[cid] >> (wp * 8)) & wm : 0u;
+    // this warp's 8 lanes of the vertex's staged row: 16 B of levels, 32 B of parents
+    uint4 lv8 = make_uint4(0, 0, 0, 0);
+    int4 pa0 = make_int4(0, 0, 0, 0), pa1 = pa0;
+    if (vis) {
+      lv8 = *reinterpret_cast<const uint4*>(s.L + (int64_t)cid * 64 + wp * 8);
+      if (!add) {
+        pa0 = *reinterpret_cast<const int4*>(s.P + (int64_t)cid * 64 + wp * 8);
+        pa1 = *reinterpret_cast<const int4*>(s.P + (int64_t)cid * 64 + wp * 8 + 4);
       }
-      const uint32_t vis = cid >= 0 ? (uint32_t)(s.visit[cid] >> (wp * 8)) & 0xFFu : 0u;
-      // this warp's 8 lanes of the vertex's staged row: 16 B of levels, 32 B of parents
-      uint4 lv8 = make_uint4(0, 0, 0, 0);
-      int4 pa0 = make_int4(0, 0, 0, 0), pa1 = pa0;
-      if (vis) {
-        lv8 = *reinterpret_cast<const uint4*>(s.L + (int64_t)cid * 64 + wp * 8);
-        if (!add) {
-          pa0 = *reinterpret_cast<const int4*>(s.P + (int64_t)cid * 64 + wp * 8);
-          pa1 = *reinterpret_cast<const int4*>(s.P + (int64_t)cid * 64 + wp * 8 + 4);
-        }
-      }
-      const uint32_t lw[4] = {lv8.x, lv8.y, lv8.z, lv8.w};
-      const int32_t pw[8] = {pa0.x, pa0.y, pa0.z, pa0.w, pa1.x, pa1.y, pa1.z, pa1.w};
-      const int32_t none = info == INT32_MIN ? -2 : -1;
+    }
+    const uint32_t lw[4] = {lv8.x, lv8.y, lv8.z, lv8.w};
+    const int32_t pw[8] = {pa0.x, pa0.y, pa0.z, pa0.w, pa1.x, pa1.y, pa1.z, pa1.w};
+    const int32_t none = info == INT32_MIN ? -2 : -1;
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        if (k >= nl || !in) continue;
-        const bool r = (vis >> k) & 1u;
-        const int32_t lk = (int32_t)((lw[k >> 1] >> (16 * (k & 1))) & 0xFFFFu);
-        ol[k][v] = r ? lk + base[k] + add : none;
-        op[k][v] = r ? (add ? fixed_parent : pw[k]) : none;
-      }
+    for (int k = 0; k < 8; ++k) {
+      if (!((wm >> k) & 1u) || !in) continue;
+      const bool r = (vis >> k) & 1u;
+      const int32_t lk = (int32_t)((lw[k >> 1] >> (16 * (k & 1))) & 0xFFFFu);
+      int32_t* pk = HOIST ? op[k] : s.outp[wp * 8 + k];
+      int32_t* lq = HOIST ? ol[k] : s.outl[wp * 8 + k];
+      const int32_t bk = HOIST ? base[k] : s.lane[wp * 8 + k].base;
+      lq[v] = r ? lk + bk + add : none;
+      pk[v] = r ? (add ? fixed_parent : pw[k]) : none;
     }
   }
 }
 
-// Root on an edge tree (one thread per lane): levels and parents along the walk from
-// the root to the core, direction reversed; the core vertex reached takes the last tree
-// vertex as parent.
-__global__ void batch_fixup(SlotDev* slots, int nslots) {
-  const int si = blockIdx.x;
-  if (si >= nslots) return;
-  const SlotDev& s = slots[si];
-  const int l = threadIdx.x;
-  if (l >= s.nlanes) return;
+// Root on an edge tree: levels and parents along the walk from the root to the core,
+// direction reversed; the core vertex reached takes the last tree vertex as parent.
+__device__ void fixup_lane(const SlotDev& s, int l) {
   const int32_t root = s.lane[l].root;
   if (s.vinfo[root] >= 0) return;
   int32_t* lv = s.outl[l];
@@ -606,23 +699,15 @@ __global__ void batch_fixup(SlotDev* slots, int nslots) {
   }
 }
 
-struct ResolveSeg {
-  const int32_t* list;
-  const int32_t* lup;
-  int64_t b, e;
-};
-
-// One height of the tree-up resolution for every lane of every slot: entries still at -2
-// take level(up) + 1 and parent up (Alg. 10 with levels); walk vertices are already set.
-__global__ void batch_resolve(SlotDev* slots, const ResolveSeg* segs, int nslots) {
-  const int si = blockIdx.y;
-  if (si >= nslots) return;
-  const SlotDev& s = slots[si];
-  const ResolveSeg sg = segs[si];
+// One height of the tree-up resolution for the lanes listed in `ls` (nl of them): entries
+// still at -2 take level(up) + 1 and parent up (Alg. 10 with levels); walk vertices are
+// already set. Thread t of `nt` starting at t0.
+__device__ void resolve_lanes(const SlotDev& s, const ResolveSeg& sg, const int8_t* ls, int nl, int64_t t0,
+                              int64_t nt) {
   const int64_t len = sg.e - sg.b;
-  const int64_t total = len * s.nlanes;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int l = (int)(t / len);
+  const int64_t total = len * nl;
+  for (int64_t t = t0; t < total; t += nt) {
+    const int l = ls[t / len];
     const int64_t i = sg.b + t % len;
     int32_t* lv = s.outl[l];
     int32_t* pa = s.outp[l];
@@ -633,6 +718,44 @@ __global__ void batch_resolve(SlotDev* slots, const ResolveSeg* segs, int nslots
     lv[v] = lu >= 0 ? lu + 1 : -1;
     pa[v] = lu >= 0 ? u : -1;
   }
+}
+
+__device__ int list_lanes(uint64_t mask, int8_t* ls) {
+  int n = 0;
+  while (mask) {
+    ls[n++] = (int8_t)(__ffsll((long long)mask) - 1);
+    mask &= mask - 1;
+  }
+  return n;
+}
+
+__global__ void __launch_bounds__(BT) batch_output(SlotDev* slots, int nslots) {
+  for (int si = 0; si < nslots; ++si) {
+    const SlotDev& s = slots[si];
+    write_lanes<true>(s, lanes_of(s.nlanes) & ~s.emitted);
+  }
+}
+
+// Roots on an edge tree, one thread per lane (lanes not written during the launch).
+__global__ void batch_fixup(SlotDev* slots, int nslots) {
+  const int si = blockIdx.x;
+  if (si >= nslots) return;
+  const SlotDev& s = slots[si];
+  const int l = threadIdx.x;
+  if (l >= s.nlanes || ((s.emitted >> l) & 1ull)) return;
+  fixup_lane(s, l);
+}
+
+// One height of the resolution for every lane of every slot not written during the launch.
+__global__ void batch_resolve(SlotDev* slots, const ResolveSeg* segs, int nslots) {
+  const int si = blockIdx.y;
+  if (si >= nslots) return;
+  __shared__ int8_t ls[64];
+  __shared__ int nl;
+  const SlotDev& s = slots[si];
+  if (threadIdx.x == 0) nl = list_lanes(lanes_of(s.nlanes) & ~s.emitted, ls);
+  __syncthreads();
+  resolve_lanes(s, segs[si], ls, nl, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
 }
 
 // The Alg. 9 walk of a lane's root to its core vertex: start (core id, -1: nothing to
@@ -738,7 +861,9 @@ void enqueue_batch(SlotDev* d_slots, SlotCtl* d_ctl, BatchCtl* d_bc, ResolveSeg*
   batch_lanes<<<ns, 64, 0, st>>>(d_slots, ns);
   batch_init<<<ns, 64, 0, st>>>(d_slots, d_ctl, ns);
   int nsl = ns;
-  void* kargs[] = {(void*)&d_slots, (void*)&d_ctl, (void*)&nsl, (void*)&d_bc};
+  const ResolveSeg* segs = d_seg;
+  int mh = maxh;
+  void* kargs[] = {(void*)&d_slots, (void*)&d_ctl, (void*)&nsl, (void*)&d_bc, (void*)&segs, (void*)&mh};
   cudaLaunchCooperativeKernel((void*)batch_run, dim3(grid), dim3(BT), kargs, 0, st);
   batch_output<<<ogrid, BT, 0, st>>>(d_slots, ns);
   batch_fixup<<<ns, 64, 0, st>>>(d_slots, ns);
@@ -831,7 +956,7 @@ int batch_launch(BatchCtx* ctx, const SlotSpec* specs, int nspecs, int sm_share,
       d.outp[l] = sp.outp[l];
       d.outl[l] = sp.outl[l];
     }
-    hc[i] = SlotCtl{{0, 0}, 0, 0, 0, DIR_TD, 0, 0};
+    hc[i] = SlotCtl{{0, 0}, 0, 0, 0, DIR_TD, 0, 0, 0, 0};
     // heights are processed top down; each slot walks its own graph's segments
     for (int h = 0; h < maxh; ++h) {
       ResolveSeg sg{g->resolve_list, g->resolve_up, 0, 0};

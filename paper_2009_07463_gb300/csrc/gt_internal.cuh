@@ -192,7 +192,11 @@ struct SlotSpec {
 // launch moves published entries into free lanes of the slots that share the mailbox,
 // raises `taken`, and sets `closed` once it will take no more. Lives in page-locked host
 // memory mapped into the device.
+// The same mailbox carries the launch's early completions: a lane whose traversal ended
+// while others continue has its results written at the next level boundary, and its bit
+// is then set in done[lane word].
 constexpr int MAILBOX_CAP = 256;
+constexpr int MAILBOX_WORDS = 256;  // lane words of one launch
 struct BatchMailbox {
   int32_t count;   // host: entries published
   int32_t taken;   // device: entries admitted into lanes
@@ -200,9 +204,12 @@ struct BatchMailbox {
   int32_t pad;
   struct Entry {
     int64_t root;
-    int32_t* outp;  // device int32[n]
+    int32_t* outp;    // device int32[n]
     int32_t* outl;
+    int32_t lane_id;  // device: lane word * 64 + lane the entry was admitted into
+    int32_t pad;
   } e[MAILBOX_CAP];
+  uint64_t done[MAILBOX_WORDS];  // device: lanes whose results are in their buffers
 };
 int run_batch(gt_graph* const* graphs, int ngraphs, const int64_t* roots, const int32_t* roots_per_graph,
               int32_t* const* parent, int32_t* const* level, cudaStream_t s);

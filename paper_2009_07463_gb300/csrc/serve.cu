@@ -81,12 +81,25 @@ struct Flight {
   std::vector<Query*> queries;
   std::vector<int> slots;
   std::vector<QueryDone> done;
-  BatchMailbox* mb = nullptr;  // batched: roots joining while it runs (host address)
+  BatchMailbox* mb = nullptr;  // batched: joining roots and early completions (host address)
   int capacity = 0;            // free lanes the launch can still fill
   std::vector<Query*> late;    // queries published in mb, in mailbox order
+  std::vector<Query*> lane_q;  // batched: query of each lane (word * 64 + lane); null once completed
+  std::vector<uint64_t> seen;  // done bits already handled, per lane word
+  int late_seen = 0;           // mailbox entries already placed in lane_q
 };
 
 double ema(double old, double x) { return old > 0 ? 0.8 * old + 0.2 * x : x; }
+
+// Places mailbox entries admitted since the last look into their lanes.
+void map_admitted(Flight* f, int taken) {
+  volatile BatchMailbox* vm = f->mb;
+  taken = std::max(0, std::min(taken, (int)f->late.size()));
+  for (; f->late_seen < taken; ++f->late_seen) {
+    const int id = vm->e[f->late_seen].lane_id;
+    if (id >= 0 && id < (int)f->lane_q.size()) f->lane_q[id] = f->late[f->late_seen];
+  }
+}
 
 }  // namespace
 }  // namespace gt
@@ -108,13 +121,53 @@ struct gt_server {
   std::vector<gt::BatchMailbox*> mbox, mbox_dev;  // per stream: pinned mailbox (host / device address)
   int64_t used_bytes = 0;
   // statistics
-  int64_t submitted = 0, completed = 0, failed = 0, batches = 0, joined = 0;
+  int64_t submitted = 0, completed = 0, failed = 0, batches = 0, joined = 0, early = 0;
   double t_first = 0, t_last = 0;
   std::vector<double> lat_us;
 };
 
 namespace gt {
 namespace {
+
+void complete(gt_server* s, Query* q, int rc, double t) {
+  q->done = true;
+  q->rc = rc;
+  q->t_done = t;
+  s->lat_us.push_back(t - q->t_submit);
+  if (rc) s->failed++;
+  s->completed++;
+  s->t_last = t;
+}
+
+// Lanes of a running batched launch whose results are already in their buffers (done
+// bits in the mailbox) complete now. Caller holds the lock.
+void collect_early(gt_server* s, Flight* f) {
+  volatile BatchMailbox* vm = f->mb;
+  const int words = (int)f->seen.size();
+  std::vector<uint64_t> d(words);
+  bool any = false;
+  for (int w = 0; w < words; ++w) {
+    d[w] = vm->done[w] & ~f->seen[w];
+    any |= d[w] != 0;
+  }
+  if (!any) return;
+  std::atomic_thread_fence(std::memory_order_acquire);
+  map_admitted(f, vm->taken);  // a lane is admitted before its done bit is set
+  std::atomic_thread_fence(std::memory_order_acquire);
+  const double t = now_us();
+  for (int w = 0; w < words; ++w) {
+    f->seen[w] |= d[w];
+    for (uint64_t b = d[w]; b; b &= b - 1) {
+      const int id = w * 64 + __builtin_ctzll(b);
+      Query* q = f->lane_q[id];
+      if (!q) continue;
+      f->lane_q[id] = nullptr;
+      complete(s, q, GT_OK, t);
+      s->early++;
+    }
+  }
+  s->cv_done.notify_all();
+}
 
 // Host callback after one single-root traversal of a single-mode flight.
 void CUDART_CB on_query_done(void* arg) {
@@ -126,13 +179,7 @@ void CUDART_CB on_query_done(void* arg) {
   GraphEntry& ge = s->graphs[f->gid];
   ge.est_single_us = ema(ge.est_single_us, t - f->t_prev);
   f->t_prev = t;
-  Query* q = d->q;
-  q->done = true;
-  q->rc = GT_OK;
-  q->t_done = t;
-  s->lat_us.push_back(t - q->t_submit);
-  s->completed++;
-  s->t_last = t;
+  complete(s, d->q, GT_OK, t);
   if (--f->remaining == 0) {
     ge.single_busy = false;
     s->flights[f->stream] = nullptr;
@@ -151,22 +198,21 @@ void CUDART_CB on_flight_done(void* arg) {
   GraphEntry& ge = s->graphs[f->gid];
   if (!f->slots.empty()) ge.est_word_us = ema(ge.est_word_us, (t - f->t_launch) / f->slots.size());
   for (int k : f->slots) ge.free_slots.push_back(k);
-  // the launch has finished: the mailbox counts are final
-  size_t taken = 0;
   if (f->mb) {
+    // the launch has finished: the mailbox is final. Lanes not completed early (all of
+    // them if the launch failed before writing them) complete now.
     const int32_t tk = ((volatile BatchMailbox*)f->mb)->taken;
-    taken = (size_t)std::max<int32_t>(0, std::min<int32_t>(tk, (int32_t)f->late.size()));
-  }
-  for (size_t i = 0; i < taken; ++i) f->queries.push_back(f->late[i]);
-  for (size_t i = f->late.size(); i > taken; --i) ge.pending.push_front(f->late[i - 1]);  // not admitted: back in line
-  s->joined += (int64_t)taken;
-  for (Query* q : f->queries) {
-    q->done = true;
-    q->rc = rc;
-    q->t_done = t;
-    s->lat_us.push_back(t - q->t_submit);
-    if (rc) s->failed++;
-    s->completed++;
+    const size_t taken = (size_t)std::max<int32_t>(0, std::min<int32_t>(tk, (int32_t)f->late.size()));
+    map_admitted(f, (int)taken);
+    for (size_t i = f->late.size(); i > taken; --i) ge.pending.push_front(f->late[i - 1]);  // not admitted: back in line
+    s->joined += (int64_t)taken;
+    for (Query*& q : f->lane_q)
+      if (q) {
+        complete(s, q, rc, t);
+        q = nullptr;
+      }
+  } else {
+    for (Query* q : f->queries) complete(s, q, rc, t);
   }
   s->t_last = t;
   s->flights[f->stream] = nullptr;
@@ -221,7 +267,10 @@ void scheduler(gt_server* s) {
       else if (free_stream < 0) free_stream = (int)i;
     }
     if (s->stop && busy == 0) break;
-    // pending roots of a graph with a batched launch in flight join its free lanes
+    // lanes of running batched launches that have finished complete at once; pending
+    // roots of a graph with a batched launch in flight join its free lanes
+    for (Flight* f : s->flights)
+      if (f && !f->single && f->mb) collect_early(s, f);
     for (Flight* f : s->flights) {
       if (!f || f->single || !f->mb || s->stop) continue;
       volatile BatchMailbox* vm = f->mb;
@@ -234,6 +283,7 @@ void scheduler(gt_server* s) {
         vm->e[k].root = q->root;
         vm->e[k].outp = q->parent;
         vm->e[k].outl = q->level;
+        vm->e[k].lane_id = -1;
         std::atomic_thread_fence(std::memory_order_release);  // entry before count
         vm->count = k + 1;
         f->late.push_back(q);
@@ -366,14 +416,20 @@ void scheduler(gt_server* s) {
     cudaStream_t st = s->streams[free_stream];
     BatchCtx* ctx = &s->ctxs[free_stream];
     const int share = std::max(1, s->sms / (int)s->streams.size());
+    // with free lanes and join_levels > 0 the launch takes roots through the stream's
+    // mailbox, and reports there the lanes that end before the launch does
     f->capacity = s->cfg.join_levels > 0 ? std::min<int>(MAILBOX_CAP, words * 64 - (int)take) : 0;
     BatchMailbox* mb_dev = nullptr;
     if (f->capacity > 0) {
       f->mb = s->mbox[free_stream];
+      f->lane_q.assign((size_t)words * 64, nullptr);
+      for (size_t i = 0; i < take; ++i) f->lane_q[i] = f->queries[i];
+      f->seen.assign(words, 0);
       volatile BatchMailbox* vm = f->mb;
       vm->count = 0;
       vm->taken = 0;
       vm->closed = 0;
+      for (int w = 0; w < words; ++w) vm->done[w] = 0;
       std::atomic_thread_fence(std::memory_order_release);
       mb_dev = s->mbox_dev[free_stream];
     }
@@ -567,6 +623,7 @@ GT_API int gt_serve_get_stats(gt_server_t s, gt_serve_stats* out) {
   out->failed = s->failed;
   out->batches = s->batches;
   out->joined = s->joined;
+  out->early = s->early;
   for (auto* f : s->flights) out->inflight += f ? 1 : 0;
   for (auto& ge : s->graphs) out->pending += (int64_t)ge.pending.size();
   out->device_bytes = s->used_bytes;
@@ -590,7 +647,7 @@ GT_API int gt_serve_reset_stats(gt_server_t s) {
   if (!s) return GT_EINVAL;
   std::lock_guard<std::mutex> lk(s->mu);
   s->lat_us.clear();
-  s->submitted = s->completed = s->failed = s->batches = s->joined = 0;
+  s->submitted = s->completed = s->failed = s->batches = s->joined = s->early = 0;
   s->t_first = s->t_last = 0;
   return GT_OK;
 }

@@ -154,3 +154,38 @@ def test_roots_join_a_running_launch(torch):
         if joined > 0:
             break
     assert joined > 0, "no root joined a running launch in three tries"
+
+
+def test_lanes_complete_before_their_launch_ends(torch):
+    # a long cycle next to a shallow R-MAT component: a batched launch starts from a cycle
+    # root (thousands of levels); R-MAT roots arriving meanwhile join its free lanes, end
+    # within a few levels, and are written and completed while the launch still runs;
+    # every result equals the oracle's
+    s, cyc = 13, 6000
+    base = 1 << s
+    n = base + cyc
+    ring = np.arange(cyc, dtype=np.int64) + base
+    e = np.concatenate([graphgen.rmat_edges(s, 16, seed=95), np.stack([ring, np.roll(ring, 1)], axis=1)])
+    og = OracleGraph(e, n)
+    g = gt.gt_graph_build(e, n)
+    roots = [base + 17] + graphgen.pick_roots(96, base, 8, og.degree()[:base]).tolist()
+    early = joined = 0
+    for attempt in range(3):
+        srv = gt.Server(streams=1, max_batch_roots=64, policy=gt.GT_SERVE_BATCHED, join_levels=64)
+        gid = srv.add_graph(g)
+        bufs = [(torch.empty(n, dtype=torch.int32, device="cuda"), torch.empty(n, dtype=torch.int32, device="cuda"))
+                for _ in roots]
+        tickets = [srv.submit(gid, roots[0], *bufs[0])]
+        time.sleep(0.0002)
+        tickets += [srv.submit(gid, r, *b) for r, b in zip(roots[1:], bufs[1:])]
+        for t in tickets:
+            assert srv.poll(t, 60000) == gt.GT_OK
+        st = srv.stats()
+        early, joined = st["early"], st["joined"]
+        for r, (p, l) in zip(roots, bufs):
+            want_l, want_p = og.bfs(r)
+            assert np.array_equal(l.cpu().numpy(), want_l) and np.array_equal(p.cpu().numpy(), want_p), f"root {r}"
+        srv.destroy()
+        if early > 0:
+            break
+    assert joined > 0 and early > 0, f"no lane completed before its launch ended in three tries ({joined} joined)"
