@@ -34,6 +34,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+E2E_CHUNK = 8  # roots per gt_bfs_roots call in the end-to-end pass
 METRIC = "harmonic-mean GTEPS over 64 roots at R-MAT scale 26; served queries/s and p99"
 UNIT = "GTEPS"
 
@@ -400,19 +401,34 @@ def main():
         out["plain_do_bfs"] = {"value": round(hmean(pg), 3), "unit": UNIT,
                                "et_over_plain": round(hm / hmean(pg), 3) if hmean(pg) else None}
 
-        # end to end through the C-ABI: host (pinned) output buffers, copies inside the timing
-        hp = torch.empty(n, dtype=torch.int32).pin_memory()
-        hl = torch.empty(n, dtype=torch.int32).pin_memory()
+        # end to end through the C-ABI: host (pinned) output buffers, copies inside the timing.
+        # gt_bfs_roots takes E2E_CHUNK roots per call, each with its own host buffers, and
+        # overlaps the copy of one result with the traversal of the next
+        hb = [(torch.empty(n, dtype=torch.int32).pin_memory(), torch.empty(n, dtype=torch.int32).pin_memory())
+              for _ in range(E2E_CHUNK)]
+        g.bfs_roots(roots[:E2E_CHUNK], [b[0] for b in hb], [b[1] for b in hb], stream=stream)  # first use: staging
+        e_time, e_tup = 0.0, 0.0
+        for c0 in range(0, len(roots), E2E_CHUNK):
+            chunk = roots[c0:c0 + E2E_CHUNK]
+            t = time.perf_counter()
+            g.bfs_roots(chunk, [b[0] for b in hb[:len(chunk)]], [b[1] for b in hb[:len(chunk)]], stream=stream)
+            e_time += time.perf_counter() - t  # returns once every result is in host memory
+            e_tup += sum(tuples[c0:c0 + len(chunk)])
+        hp, hl = hb[0]
         g.bfs(roots[0], hp, hl, stream=stream)
         eg = []
         for i, r in enumerate(roots):
             t = time.perf_counter()
             g.bfs(r, hp, hl, stream=stream)  # returns once the results are in host memory
             eg.append(tuples[i] / (time.perf_counter() - t) / 1e9)
-        out["e2e"] = {"value": round(hmean(eg), 3), "unit": UNIT, "h2d_bytes_per_step": 8 * len(roots),
+        out["e2e"] = {"value": round(e_tup / e_time / 1e9, 3), "unit": UNIT, "h2d_bytes_per_step": 8 * len(roots),
                       "d2h_bytes_per_step": 8 * n * len(roots),
-                      "how": "gt_bfs with pinned host parent/level buffers; D2H copy and stream sync inside each "
-                             "timed call; root passed by value"}
+                      "how": f"gt_bfs_roots, {E2E_CHUNK} roots per call into pinned host parent/level buffers (one "
+                             "pair per root); host clock around each call, which returns once every result is in "
+                             "host memory; traversed tuples / summed call time",
+                      "single_call": {"value": round(hmean(eg), 3),
+                                      "how": "gt_bfs per root into one pinned pair (returns after its copy); "
+                                             "harmonic mean"}}
 
         if oracle is not None:
             oracle[2].set()  # the timed and e2e passes are done: the CPU leg may start

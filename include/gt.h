@@ -139,6 +139,17 @@ GT_API int gt_graph_set_tuning(gt_graph_t g, const gt_tuning* t);
  * staged on the device and copied back. With host memory the call returns after `stream`
  * has finished. */
 GT_API int gt_bfs(gt_graph_t g, int64_t root, int32_t* parent, int32_t* level, void* stream);
+/* k edge-tree BFS (as gt_bfs, Alg. 9) from roots[0..k-1] (host array), in that order on
+ * `stream`; root i writes parent[i] and level[i] (int32[n] each, both device or both host
+ * memory; roots may differ). Host results are staged on the device (two staging pairs,
+ * 16 B x n, allocated on first use and kept with the handle) and copied to the host by the
+ * copy engine on a stream of the handle while the next root is traversed, so the
+ * host-link transfer of one result overlaps the traversal of the next. Returns after
+ * every host result is in place (device results: stream-ordered on `stream`). GT_EINVAL
+ * for a null argument, k < 0, a root outside [0, n) or a root whose two outputs are in
+ * different memories (nothing is run then). */
+GT_API int gt_bfs_roots(gt_graph_t g, const int64_t* roots, int32_t k, int32_t* const* parent,
+                        int32_t* const* level, void* stream);
 /* The same contract on the unsplit graph (plain direction-optimizing BFS, Alg. 1); the
  * comparison baseline. GT_ENOTSUP if the handle was built with keep_plain = 0. */
 GT_API int gt_bfs_plain(gt_graph_t g, int64_t root, int32_t* parent, int32_t* level, void* stream);

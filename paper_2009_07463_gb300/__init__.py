@@ -83,6 +83,7 @@ def lib():
                 "gt_graph_set_tuning": (ctypes.c_int, [p, p]),
                 "gt_bfs": (ctypes.c_int, [p, i64, p, p, p]),
                 "gt_bfs_plain": (ctypes.c_int, [p, i64, p, p, p]),
+                "gt_bfs_roots": (ctypes.c_int, [p, p, i32, p, p, p]),
                 "gt_bfs_trace": (ctypes.c_int, [p, p, i32, p]),
                 "gt_bfs_timing": (ctypes.c_int, [p, p]),
                 "gt_bfs_csr_noalloc": (ctypes.c_int, [p, p, i64, i64, p, p, p]),
@@ -226,6 +227,19 @@ class Graph:
         _check(f(self._h, int(root), _out(parent, self.n, "parent"), _out(level, self.n, "level"), _stream(stream)),
                "gt_bfs_plain" if plain else "gt_bfs")
         return parent, level
+
+    def bfs_roots(self, roots, parents, levels, stream=None):
+        """gt_bfs_roots: one edge-tree BFS per root, in order; parents[i] / levels[i] receive
+        root i's result (int32[n] each, device or host). Host results are copied back while
+        the next root is traversed; returns once they are all in place."""
+        k = len(roots)
+        if len(parents) != k or len(levels) != k:
+            raise ValueError("one parent and one level buffer per root")
+        ra = (ctypes.c_int64 * max(1, k))(*[int(r) for r in roots])
+        pp = (ctypes.c_void_p * max(1, k))(*[_out(x, self.n, "parent") for x in parents])
+        lp = (ctypes.c_void_p * max(1, k))(*[_out(x, self.n, "level") for x in levels])
+        _check(lib().gt_bfs_roots(self._h, ra, k, pp, lp, _stream(stream)), "gt_bfs_roots")
+        return parents, levels
 
     def bfs_plain(self, root: int, parent=None, level=None, stream=None):
         return self.bfs(root, parent, level, stream, plain=True)

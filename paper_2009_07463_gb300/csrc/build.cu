@@ -451,6 +451,14 @@ void free_graph(gt_graph* g) {
   cudaFree(g->resolve_list);
   cudaFree(g->resolve_up);
   cudaFree(g->scratch_out);
+  cudaFree(g->pipe_out);
+  g->pipe_out = nullptr;
+  if (g->copy_stream) cudaStreamDestroy(g->copy_stream);
+  g->copy_stream = nullptr;
+  for (cudaEvent_t& e : g->pipe_ev) {
+    if (e) cudaEventDestroy(e);
+    e = nullptr;
+  }
   delete[] g->resolve_ptr_host;
   g->resolve_ptr_host = nullptr;
 }

@@ -5,6 +5,7 @@
 
 #include <new>
 #include <string>
+#include <vector>
 
 #include "gt_device.cuh"
 #include "gt_internal.cuh"
@@ -124,6 +125,76 @@ int bfs_common(gt_graph_t g, bool et, int64_t root, int32_t* parent, int32_t* le
   rc = cuda_fail(cudaMemcpyAsync(parent, dp, sizeof(int32_t) * g->n, cudaMemcpyDeviceToHost, s), "copy parent");
   if (!rc) rc = cuda_fail(cudaMemcpyAsync(level, dl, sizeof(int32_t) * g->n, cudaMemcpyDeviceToHost, s), "copy level");
   if (!rc) rc = cuda_fail(cudaStreamSynchronize(s), "bfs sync");
+  return rc;
+}
+
+// k edge-tree traversals in order on `s`. Roots with device outputs write them directly.
+// Roots with host outputs write a device staging pair (two pairs, alternating), and the
+// copy engine moves it to the host on the graph's copy stream while the traversal of the
+// next root already runs; the next root is always enqueued before the copy of the previous
+// one, so pageable copies (which block the calling thread) overlap it too.
+int bfs_roots(gt_graph_t g, const int64_t* roots, int32_t k, int32_t* const* parent, int32_t* const* level,
+              cudaStream_t s) {
+  std::vector<char> host(k);
+  bool any_host = false;
+  for (int32_t i = 0; i < k; ++i) {
+    const int wp = where(parent[i]), wl = where(level[i]);
+    if (wp < 0 || wl < 0 || wp != wl) {
+      set_error("gt_bfs_roots: null output, or parent and level of a root in different memories");
+      return GT_EINVAL;
+    }
+    host[i] = wp == 0;
+    any_host |= wp == 0;
+  }
+  int rc = GT_OK;
+  if (any_host) {
+    if (!g->pipe_out) rc = device_malloc(g, (void**)&g->pipe_out, sizeof(int32_t) * 4 * g->n);
+    if (!rc && !g->copy_stream)
+      rc = cuda_fail(cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking), "copy stream");
+    for (int i = 0; i < 4 && !rc; ++i)
+      if (!g->pipe_ev[i]) rc = cuda_fail(cudaEventCreateWithFlags(&g->pipe_ev[i], cudaEventDisableTiming), "event");
+    if (rc) return rc;
+  }
+  cudaStream_t cs = g->copy_stream;
+  cudaEvent_t* ev_out = g->pipe_ev;       // staging pair b written
+  cudaEvent_t* ev_copied = g->pipe_ev + 2;  // staging pair b copied to the host
+  std::vector<int> pair(k, -1);
+  bool used[2] = {false, false};
+  int next_pair = 0;
+  auto launch = [&](int32_t i) -> int {
+    if (!host[i]) return run_bfs(g, g->core, true, roots[i], parent[i], level[i], s);
+    const int b = next_pair;
+    next_pair ^= 1;
+    pair[i] = b;
+    if (used[b]) {
+      const int r = cuda_fail(cudaStreamWaitEvent(s, ev_copied[b], 0), "wait copy");
+      if (r) return r;
+    }
+    used[b] = true;
+    int32_t* dp = g->pipe_out + (int64_t)(2 * b) * g->n;
+    int r = run_bfs(g, g->core, true, roots[i], dp, dp + g->n, s);
+    if (!r) r = cuda_fail(cudaEventRecord(ev_out[b], s), "record output");
+    return r;
+  };
+  auto copy = [&](int32_t i) -> int {
+    const int b = pair[i];
+    const int32_t* dp = g->pipe_out + (int64_t)(2 * b) * g->n;
+    const size_t bytes = sizeof(int32_t) * (size_t)g->n;
+    int r = cuda_fail(cudaStreamWaitEvent(cs, ev_out[b], 0), "wait output");
+    if (!r) r = cuda_fail(cudaMemcpyAsync(parent[i], dp, bytes, cudaMemcpyDeviceToHost, cs), "copy parent");
+    if (!r) r = cuda_fail(cudaMemcpyAsync(level[i], dp + g->n, bytes, cudaMemcpyDeviceToHost, cs), "copy level");
+    if (!r) r = cuda_fail(cudaEventRecord(ev_copied[b], cs), "record copy");
+    return r;
+  };
+  if (k > 0) rc = launch(0);
+  for (int32_t i = 0; i < k && !rc; ++i) {
+    if (i + 1 < k) rc = launch(i + 1);
+    if (!rc && host[i]) rc = copy(i);
+  }
+  if (any_host) {
+    const int r = cuda_fail(cudaStreamSynchronize(cs), "copy sync");
+    if (!rc) rc = r;
+  }
   return rc;
 }
 
@@ -262,6 +333,22 @@ GT_API int gt_graph_set_tuning(gt_graph_t g, const gt_tuning* t) {
 
 GT_API int gt_bfs(gt_graph_t g, int64_t root, int32_t* parent, int32_t* level, void* stream) {
   return bfs_common(g, true, root, parent, level, stream);
+}
+
+GT_API int gt_bfs_roots(gt_graph_t g, const int64_t* roots, int32_t k, int32_t* const* parent,
+                        int32_t* const* level, void* stream) {
+  if (!g || k < 0 || (k > 0 && (!roots || !parent || !level))) {
+    set_error("gt_bfs_roots: null argument or k < 0");
+    return GT_EINVAL;
+  }
+  for (int32_t i = 0; i < k; ++i)
+    if (roots[i] < 0 || roots[i] >= g->n) {
+      set_error("gt_bfs_roots: root outside [0, n)");
+      return GT_EINVAL;
+    }
+  int rc = cuda_fail(cudaSetDevice(g->device), "cudaSetDevice");
+  if (rc) return rc;
+  return bfs_roots(g, roots, k, parent, level, (cudaStream_t)stream);
 }
 
 GT_API int gt_bfs_plain(gt_graph_t g, int64_t root, int32_t* parent, int32_t* level, void* stream) {

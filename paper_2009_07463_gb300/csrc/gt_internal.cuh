@@ -132,6 +132,11 @@ struct gt_graph {
   gt::View core;   // core CSR + traversal state
   gt::View plain;  // full CSR + traversal state (keep_plain)
   int32_t* scratch_out = nullptr;  // device staging when the caller passes host outputs
+  // gt_bfs_roots with host outputs: two device staging pairs (parent, level; 4n int32), the
+  // stream their copies to the host run on, and events (output written / copied, per pair)
+  int32_t* pipe_out = nullptr;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t pipe_ev[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaStream_t last_stream = nullptr;
   gt::BfsCtl* last_ctl = nullptr;
   // CUDA graphs of the level loop, one per view, instantiated lazily

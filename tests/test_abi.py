@@ -62,6 +62,7 @@ def test_defaults_and_errors_without_gpu():
     assert L.gt_graph_build(None, 5, 10, None, None, ctypes.byref(h)) == gt.GT_EINVAL
     assert L.gt_graph_build(None, 0, 0, None, None, ctypes.byref(h)) == gt.GT_EINVAL
     assert L.gt_bfs(None, 0, None, None, None) == gt.GT_EINVAL
+    assert L.gt_bfs_roots(None, None, 0, None, None, None) == gt.GT_EINVAL
     assert b"n <= 2^31" in L.gt_last_error() or L.gt_last_error()
     # server configuration is checked before the server touches a device
     c = gt.gt_serve_config()

@@ -267,3 +267,39 @@ def test_scale22_config(torch_cuda):
             pa = torch.from_numpy(got[1]).cuda()
             bfs_certificate(ed, lv, pa, r)
             assert gt.gt_count_traversed(ed, lv) == int(((got[0][e[:, 0]] >= 0) & (got[0][e[:, 1]] >= 0)).sum())
+
+
+def test_bfs_roots_pipelined_outputs(torch_cuda):
+    torch = torch_cuda
+    # gt_bfs_roots: several roots in one call with pinned host, pageable host and device
+    # outputs mixed (the two device staging pairs are reused more than once); every result
+    # equals the oracle's
+    s = 13
+    n = 1 << s
+    e = graphgen.rmat_edges(s, 16, seed=61)
+    og = OracleGraph(e, n)
+    g = gt.gt_graph_build(e, n)
+    roots = graphgen.pick_roots(62, n, 7, og.degree()).tolist()
+    kinds = ["pinned", "pageable", "device", "pinned", "pinned", "pageable", "device"]
+    bufs = []
+    for k in kinds:
+        if k == "pinned":
+            bufs.append((torch.full((n,), 7, dtype=torch.int32).pin_memory(), torch.full((n,), 7, dtype=torch.int32).pin_memory()))
+        elif k == "pageable":
+            bufs.append((np.full(n, 7, dtype=np.int32), np.full(n, 7, dtype=np.int32)))
+        else:
+            bufs.append((torch.full((n,), 7, dtype=torch.int32, device="cuda"),
+                         torch.full((n,), 7, dtype=torch.int32, device="cuda")))
+    g.bfs_roots(roots, [b[0] for b in bufs], [b[1] for b in bufs])
+    torch.cuda.synchronize()
+    for r, k, (p, l) in zip(roots, kinds, bufs):
+        want_l, want_p = og.bfs(r)
+        got_p = p if isinstance(p, np.ndarray) else p.cpu().numpy()
+        got_l = l if isinstance(l, np.ndarray) else l.cpu().numpy()
+        assert np.array_equal(got_l, want_l), f"level mismatch (root {r}, {k})"
+        assert np.array_equal(got_p, want_p), f"parent mismatch (root {r}, {k})"
+    with pytest.raises(gt.GtError):
+        g.bfs_roots([n], [bufs[0][0]], [bufs[0][1]])  # root out of range
+    with pytest.raises(gt.GtError):
+        g.bfs_roots([0], [bufs[0][0]], [bufs[2][1]])  # host parent, device level
+    g.free()
