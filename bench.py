@@ -35,6 +35,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 E2E_CHUNK = 8  # roots per gt_bfs_roots call in the end-to-end pass
+HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e nominal bandwidth, reported beside the measured copy peak
 METRIC = "harmonic-mean GTEPS over 64 roots at R-MAT scale 26; served queries/s and p99"
 UNIT = "GTEPS"
 
@@ -477,6 +478,7 @@ def main():
         trf = traffic_from_profiles("bfs_bu")
         out["roofline"] = {"bound": "hbm", "kernel": "bfs_bu_gather+bfs_bu_scan", "achieved": round(bu_gbs, 1), "peak": peak,
                            "peak_source": peak_src, "unit": "GB/s", "frac": round(bu_gbs / peak, 4),
+                           "peak_nominal": HBM_NOMINAL_GBS, "frac_nominal": round(bu_gbs / HBM_NOMINAL_GBS, 4),
                            "traffic": trf, "launches": bu_n,
                            "dram_achieved": round(trf / (bu_t / max(bu_n, 1) * 1e-3) / 1e9, 1) if trf and bu_t > 0 else None,
                            "dram_frac": round(trf / (bu_t / max(bu_n, 1) * 1e-3) / 1e9 / peak, 4) if trf and bu_t > 0 else None,
