@@ -13,7 +13,11 @@
 // SMs). Graphs are admitted against an HBM budget
 // (graph storage + one lane word of batch storage); more lane-word storage is taken
 // while the budget allows. Completion is signalled by a host callback on the stream,
-// which stamps every query's latency (submit -> results in the caller's buffers).
+// which stamps every query's latency (submit -> results in the caller's buffers). With
+// join_levels > 0, roots submitted while a batched launch of their graph runs are
+// published in a page-locked mailbox and join its free lanes at a level boundary; such a
+// launch also reports in the mailbox each lane whose results are written before it ends,
+// and the scheduler completes those queries at once.
 #include <string.h>
 
 #include <algorithm>
