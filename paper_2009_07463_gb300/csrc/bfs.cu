@@ -1,8 +1,8 @@
 // bfs.cu -- direction-optimizing BFS (Alg. 1) on a CSR view, and the edge-tree steps
 // around it (Alg. 9: root walk to the core, BFS_CORE, edge-tree resolution).
 //
-// Per-vertex state is one 64-bit word (level << 32 | parent's vertex id), UNVISITED = all
-// ones. Views of the core use core ids for traversal and vertex ids for parents.
+// Per-vertex state is one 64-bit word (level << 32 | parent's view id), UNVISITED = all
+// ones; the output pass of the core view maps parents from core ids to vertex ids.
 // Top-down (Alg. 1 TOP-DOWN): every frontier edge to a vertex that was not visited at
 // the start of the level does atomicMin(state, (L+1) << 32 | v); the smallest packed
 // value wins, i.e. level L+1 with the smallest frontier neighbour as parent, and the
@@ -37,7 +37,6 @@ struct BfsArgs {
   int32_t* queues;  // [2][NBINS][n]
   int32_t* ulist;
   const int4* pre;         // adjacency prefix records (null: none)
-  const int32_t* new2old;  // view id -> vertex id (null: the view's ids are vertex ids)
   BfsCtl* ctl;
   int32_t td_warp_min;
   int32_t td_cta_min;
@@ -59,7 +58,6 @@ BfsArgs make_args(const View& v, const gt_tuning& t) {
   a.queues = v.queues;
   a.ulist = v.ulist;
   a.pre = v.pre;
-  a.new2old = v.new2old;
   a.ctl = v.ctl;
   a.td_warp_min = std::max(1, t.td_warp_min);
   a.td_cta_min = std::max(a.td_warp_min, t.td_cta_min);
@@ -73,11 +71,8 @@ __device__ __forceinline__ int32_t* queue_of(const BfsArgs& a, int set, int bin)
   return a.queues + ((int64_t)(set * NBINS + bin)) * (a.n > 0 ? a.n : 1);
 }
 
-// The state keeps parents as vertex ids, so the output pass needs no translation. The
-// core relabel is monotone, so the smallest vertex id is also the smallest view id.
-__device__ __forceinline__ uint32_t orig_of(const BfsArgs& a, int32_t v) {
-  return a.new2old ? (uint32_t)a.new2old[v] : (uint32_t)v;
-}
+// The state keeps parents as view ids. The core relabel is monotone, so the smallest
+// core id is also the smallest vertex id, and the traversal never needs the mapping.
 
 __device__ __forceinline__ int bin_of(const BfsArgs& a, int64_t d) {
   return d <= a.td_warp_min ? 0 : (d <= a.td_cta_min ? 1 : (d <= a.td_grid_min ? 2 : 3));
@@ -213,7 +208,7 @@ __device__ __forceinline__ void block_commit(const BfsArgs& a, int64_t n_found, 
 __device__ __forceinline__ void td_edges(const BfsArgs& a, uint32_t* vis, int nxt, int32_t v, uint64_t hi,
                                          int64_t s, int64_t e, int64_t first, int64_t stride, int64_t& nf,
                                          int64_t& mf, StageQ& sq) {
-  const uint64_t packed = hi | orig_of(a, v);
+  const uint64_t packed = hi | (uint32_t)v;
   for (int64_t k0 = s + first; k0 < e; k0 += stride * TDK) {
     int32_t w[TDK];
     uint64_t pk[TDK];
@@ -282,7 +277,7 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) bfs_td(BfsArgs a) {
           const int32_t v = q[ws + t];
           const int64_t b = a.row[v];
           d4[k] = a.row[v + 1] - b;
-          s_v[t] = (int32_t)orig_of(a, v);
+          s_v[t] = v;
           s_beg[t] = b;
           if (blockIdx.x == 0) atomicOr(&vis[v >> 5], 1u << (v & 31));
         }
@@ -376,7 +371,7 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) bfs_td(BfsArgs a) {
         v = q[i];
         rs = a.row[v];
         re = a.row[v + 1];
-        vo = (int32_t)orig_of(a, v);
+        vo = v;
         atomicOr(&vis[v >> 5], 1u << (v & 31));
       }
       const int32_t sd = (int32_t)(re - rs);
@@ -679,7 +674,7 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) bfs_bu_scan(BfsArgs a) {
     for (int j = 0; j < BU_V; ++j) {
       const bool fnd = par[j] >= 0;
       if (fnd) {
-        a.state[w[j]] = hi | orig_of(a, par[j]);
+        a.state[w[j]] = hi | (uint32_t)par[j];
         ++nf;
         mf += d[j];
       }
@@ -717,7 +712,7 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) bfs_bu_scan(BfsArgs a) {
           if (par2 < 0 && lane == 0) examined += min((int64_t)(32 * CW), e2 - b0);
         }
         if (par2 >= 0 && lane == 0) {
-          a.state[w2] = hi | orig_of(a, par2);
+          a.state[w2] = hi | (uint32_t)par2;
           atomicOr(&vn[w2 >> 5], 1u << (w2 & 31));
           ++nf;
           mf += d2;
@@ -851,7 +846,7 @@ __device__ void ctl_begin(const BfsArgs& a, int32_t start, int32_t start_level, 
   }
   c->done = 0;
   const int64_t d = a.row[start + 1] - a.row[start];
-  a.state[start] = ((uint64_t)(uint32_t)start_level << 32) | orig_of(a, start);
+  a.state[start] = ((uint64_t)(uint32_t)start_level << 32) | (uint32_t)start;
   a.vis0[start >> 5] |= 1u << (start & 31);
   const int b = bin_of(a, d);
   queue_of(a, 0, b)[0] = start;
@@ -914,15 +909,19 @@ __global__ void et_anchors(EtArgs e, const uint64_t* __restrict__ state) {
 }
 
 // Levels and parents of every vertex in vertex-id order: core vertices from the core
-// BFS state (parents already vertex ids), edge-tree vertices hanging from a core vertex
-// from their anchor's entry (Alg. 7 / Alg. 10 with levels), tree vertices hanging from a
-// tree vertex -2 ("resolve pending", see et_resolve), everything else -1.
-// Four consecutive vertices per thread: one 128-bit vinfo load, four independent
-// gathers, 128-bit stores (when n and the outputs allow).
+// BFS state (parents there are core ids, mapped to vertex ids here), edge-tree vertices
+// hanging from a core vertex from their anchor's entry (Alg. 7 / Alg. 10 with levels),
+// tree vertices hanging from a tree vertex -2 ("resolve pending", see et_resolve),
+// everything else -1. Four consecutive vertices per thread: one 128-bit vinfo load,
+// four independent gathers, 128-bit stores (when n and the outputs allow).
 __device__ __forceinline__ uint64_t et_packed(const EtArgs& e, const uint64_t* __restrict__ state, int32_t info) {
   if (info >= 0) return state[info];
   if (info != INT32_MIN && info <= -2) return e.anchor_out[-2 - info];
   return UNVISITED;
+}
+
+__device__ __forceinline__ int32_t et_parent(const EtArgs& e, uint64_t st, int32_t info) {
+  return info >= 0 ? e.new2old[(uint32_t)st] : (int32_t)(uint32_t)st;
 }
 
 __global__ void et_output(EtArgs e, const uint64_t* __restrict__ state, int32_t* __restrict__ parent,
@@ -939,7 +938,7 @@ __global__ void et_output(EtArgs e, const uint64_t* __restrict__ state, int32_t*
     for (int k = 0; k < 4; ++k) {
       const bool r = st[k] != UNVISITED;
       l[k] = r ? (int32_t)(st[k] >> 32) : (info[k] == INT32_MIN ? -2 : -1);
-      p[k] = r ? (int32_t)(uint32_t)st[k] : l[k];
+      p[k] = r ? et_parent(e, st[k], info[k]) : l[k];
     }
     reinterpret_cast<int4*>(level)[i] = make_int4(l[0], l[1], l[2], l[3]);
     reinterpret_cast<int4*>(parent)[i] = make_int4(p[0], p[1], p[2], p[3]);
@@ -950,7 +949,7 @@ __global__ void et_output(EtArgs e, const uint64_t* __restrict__ state, int32_t*
     const bool r = st != UNVISITED;
     const int32_t l = r ? (int32_t)(st >> 32) : (info == INT32_MIN ? -2 : -1);
     level[v] = l;
-    parent[v] = r ? (int32_t)(uint32_t)st : l;
+    parent[v] = r ? et_parent(e, st, info) : l;
   }
 }
 
