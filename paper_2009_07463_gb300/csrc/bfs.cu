@@ -913,9 +913,11 @@ __global__ void et_anchors(EtArgs e, const uint64_t* __restrict__ state) {
 // hanging from a core vertex from their anchor's entry (Alg. 7 / Alg. 10 with levels),
 // tree vertices hanging from a tree vertex -2 ("resolve pending", see et_resolve),
 // everything else -1. Four consecutive vertices per thread: one 128-bit vinfo load,
-// four independent gathers, 128-bit stores (when n and the outputs allow).
+// four independent gathers, 128-bit stores (when n and the outputs allow). What streams
+// through (vinfo, core state, outputs) is loaded and stored evict-first, which leaves L2
+// to the id map and the anchor array that the pass gathers from.
 __device__ __forceinline__ uint64_t et_packed(const EtArgs& e, const uint64_t* __restrict__ state, int32_t info) {
-  if (info >= 0) return state[info];
+  if (info >= 0) return __ldcs(reinterpret_cast<const unsigned long long*>(state) + info);
   if (info != INT32_MIN && info <= -2) return e.anchor_out[-2 - info];
   return UNVISITED;
 }
@@ -928,7 +930,7 @@ __global__ void et_output(EtArgs e, const uint64_t* __restrict__ state, int32_t*
                           int32_t* __restrict__ level, int vec) {
   const int64_t n4 = vec ? e.n / 4 : 0;
   for (int64_t i = gtid(); i < n4; i += gthreads()) {
-    const int4 in = reinterpret_cast<const int4*>(e.vinfo)[i];
+    const int4 in = __ldcs(reinterpret_cast<const int4*>(e.vinfo) + i);
     const int32_t info[4] = {in.x, in.y, in.z, in.w};
     uint64_t st[4];
 #pragma unroll
@@ -940,8 +942,8 @@ __global__ void et_output(EtArgs e, const uint64_t* __restrict__ state, int32_t*
       l[k] = r ? (int32_t)(st[k] >> 32) : (info[k] == INT32_MIN ? -2 : -1);
       p[k] = r ? et_parent(e, st[k], info[k]) : l[k];
     }
-    reinterpret_cast<int4*>(level)[i] = make_int4(l[0], l[1], l[2], l[3]);
-    reinterpret_cast<int4*>(parent)[i] = make_int4(p[0], p[1], p[2], p[3]);
+    __stcs(reinterpret_cast<int4*>(level) + i, make_int4(l[0], l[1], l[2], l[3]));
+    __stcs(reinterpret_cast<int4*>(parent) + i, make_int4(p[0], p[1], p[2], p[3]));
   }
   for (int64_t v = 4 * n4 + gtid(); v < e.n; v += gthreads()) {
     const int32_t info = e.vinfo[v];
