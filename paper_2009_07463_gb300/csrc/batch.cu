@@ -78,6 +78,11 @@ struct SlotDev {
                          // lanes that finish early are written and reported at once)
   uint64_t emitted;      // lanes whose results are already written
   uint64_t joined;       // lanes admitted from the mailbox during the launch
+  uint64_t joined_now;   // lanes admitted at the current level boundary
+  uint64_t young_prev;   // lanes admitted at the boundary before
+  uint64_t young;        // lanes in their first two levels after joining: pushed top-down
+                         // even when the slot pulls bottom-up (their frontier is small, and
+                         // in the pull they would miss at nearly every vertex)
   uint64_t active;
   LaneInit lane[64];
 };
@@ -372,6 +377,7 @@ __device__ void admit_roots(SlotDev* slots, SlotCtl* sctl, int nslots, const int
         }
         s.active |= bit;
         s.joined |= bit;
+        s.joined_now |= bit;
         c.alive |= bit;
       }
       s.nlanes = l + 1;
@@ -472,7 +478,10 @@ __global__ void __launch_bounds__(BT)
         // pull: every core vertex still missing lanes scans its ascending adjacency for the
         // first neighbour carrying each missing lane (min-id parents). Short adjacencies:
         // a lane each; long ones: chunks, a warp each, parents by atomicMin.
-        const uint64_t act = *(volatile const uint64_t*)&s.active;  // lanes may have joined at the last boundary
+        // Young lanes (joined one or two boundaries ago) are pushed top-down below; while
+        // there are any, next-frontier words are set by atomicOr from both sides.
+        const uint64_t yg = early ? *(volatile const uint64_t*)&s.young : 0ull;
+        const uint64_t act = *(volatile const uint64_t*)&s.active & ~yg;  // lanes may have joined at the last boundary
         for (int64_t i0 = gw * 32; i0 < s.n_lanes; i0 += nw * 32) {
           const int64_t i = i0 + lane;
           int32_t w = -1;
@@ -482,8 +491,14 @@ __global__ void __launch_bounds__(BT)
             const uint64_t miss = act & ~s.visit[w];
             if (miss) got = hits_thread(s, fc, w, miss, 0ull, s.crow[w], s.crow[w + 1]);
           }
-          if (got) fn[w] = got;
-          list_append(got != 0, w, &sctl[si].fl_n[nxt], s.fl[nxt]);
+          bool first = got != 0;
+          if (got) {
+            if (yg)
+              first = atomicOr((unsigned long long*)&fn[w], (unsigned long long)got) == 0ull;
+            else
+              fn[w] = got;
+          }
+          list_append(first, w, &sctl[si].fl_n[nxt], s.fl[nxt]);
         }
         for (int64_t it = gw; it < s.n_items; it += nw) {
           const uint64_t item = s.items[it];
@@ -497,7 +512,7 @@ __global__ void __launch_bounds__(BT)
                                      : hits_warp<true>(s, fc, w, miss, 0ull, b, e);
           bool first = false;
           if (got && lane == 0) {
-            if (whole) {
+            if (whole && !yg) {
               fn[w] = got;
               first = true;
             } else {
@@ -506,25 +521,56 @@ __global__ void __launch_bounds__(BT)
           }
           list_append(first, w, &sctl[si].fl_n[nxt], s.fl[nxt]);
         }
+        if (yg) {
+          // push of the young lanes: frontier entries carrying their bits, found 32 at a time
+          // by a ballot; a long adjacency's first chunk here, the others queued for E2
+          const int64_t nf = s_ncur[si];
+          for (int64_t j0 = gw * 32; j0 < nf; j0 += nw * 32) {
+            const int64_t j = j0 + lane;
+            int32_t v = -1;
+            uint64_t f = 0;
+            if (j < nf) {
+              v = s.fl[cur][j];
+              f = fc[v] & yg;
+            }
+            unsigned m = __ballot_sync(FULL, f != 0);
+            while (m) {
+              const int src = __ffs(m) - 1;
+              m &= m - 1;
+              const int32_t vv = __shfl_sync(FULL, v, src);
+              const uint64_t ff = __shfl_sync(FULL, f, src);
+              const int64_t b = s.crow[vv], e = s.crow[vv + 1];
+              const int64_t nch = (e - b + BATCH_CHUNK - 1) / BATCH_CHUNK;
+              if (nch > 1 && lane == 0) {
+                const unsigned long long p =
+                    atomicAdd((unsigned long long*)&sctl[si].q_n, (unsigned long long)(nch - 1));
+                for (int64_t c = 1; c < nch; ++c) s.q[p + c - 1] = ((uint64_t)vv << 32) | (uint32_t)c;
+              }
+              td_push(s, ff, s.new2old[vv], b, min(e, b + BATCH_CHUNK), fn, &sctl[si].fl_n[nxt], s.fl[nxt]);
+            }
+          }
+        }
       }
     }
     if (!grid_barrier(bc, gen)) return;
-    // ---- E2: queued chunks of long top-down adjacencies (all slots, one pass)
+    // ---- E2: queued chunks of long top-down adjacencies (all slots, one pass; in a slot
+    // pulling bottom-up, the young lanes' chunks)
     bool any_q = false;
     for (int si = 0; si < nslots; ++si) {
-      if (s_done[si] || s_dir[si] != DIR_TD) continue;
+      if (s_done[si]) continue;
       const int64_t nq = sctl[si].q_n;
       if (nq == 0) continue;
       any_q = true;
       const SlotDev& s = slots[si];
+      const uint64_t lanes = s_dir[si] == DIR_TD ? ~0ull : *(volatile const uint64_t*)&s.young;
       const int cur = s_cur[si], nxt = cur ^ 1;
       for (int64_t j = gw; j < nq; j += nw) {
         const uint64_t item = s.q[j];
         const int32_t v = (int32_t)(item >> 32);
         const int64_t rb = s.crow[v], re = s.crow[v + 1];
         const int64_t b = rb + (int64_t)(uint32_t)item * BATCH_CHUNK;
-        td_push(s, s.front[cur][v], s.new2old[v], b, min(re, b + BATCH_CHUNK), s.front[nxt], &sctl[si].fl_n[nxt],
-                s.fl[nxt]);
+        td_push(s, s.front[cur][v] & lanes, s.new2old[v], b, min(re, b + BATCH_CHUNK), s.front[nxt],
+                &sctl[si].fl_n[nxt], s.fl[nxt]);
       }
     }
     if (any_q && !grid_barrier(bc, gen)) return;
@@ -601,6 +647,11 @@ __global__ void __launch_bounds__(BT)
             s.active &= ~fin;
             atomicAdd(&bc->emit, 1);
           }
+        }
+        if (early) {  // young for the two levels after joining
+          s.young = (s.joined_now | s.young_prev) & s.active;
+          s.young_prev = s.joined_now;
+          s.joined_now = 0;
         }
       }
     }
