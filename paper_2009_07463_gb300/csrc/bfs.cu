@@ -460,27 +460,49 @@ __global__ void __launch_bounds__(BFS_THREADS) bfs_queue_from_bitmap(BfsArgs a) 
 
 // ---- bottom-up ---------------------------------------------------------------------
 // Gather: a warp reads 128 visited words with one 128-bit load per lane, copies them to
-// the next bitmap, and compacts the unvisited vertices (popc + warp sum for the
-// reservation, then one ballot per word so each word's vertices are written by
-// consecutive lanes) into a global list in ascending order (Alg. 5's block search: a
-// fully visited block costs one load).
+// the next bitmap, and compacts the unvisited vertices (popc + warp sum, one reservation
+// per CTA step, then one ballot per word so each word's vertices are written by
+// consecutive lanes) into a global list, ascending within each CTA's span (Alg. 5's block
+// search: a fully visited block costs one load). One atomic per CTA step instead of one
+// per warp: the counter is a single address that every warp would otherwise queue on.
 __global__ void __launch_bounds__(BFS_THREADS) bfs_bu_gather(BfsArgs a) {
+  __shared__ unsigned long long s_off[WARPS];
   BfsCtl* ctl = a.ctl;
   const uint4* __restrict__ vc = reinterpret_cast<const uint4*>(ctl->vcur ? a.vis1 : a.vis0);
   uint4* __restrict__ vn = reinterpret_cast<uint4*>(ctl->vcur ? a.vis0 : a.vis1);
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = gtid() >> 5, nw = gthreads() >> 5;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t nchunks = a.nwords / BU_CHUNK_WORDS;
-  for (int64_t c = gw; c < nchunks; c += nw) {
-    const uint4 w4 = __ldg(vc + c * 32 + lane);
-    vn[c * 32 + lane] = w4;
-    const uint32_t u0 = ~w4.x, u1 = ~w4.y, u2 = ~w4.z, u3 = ~w4.w;
+  // a CTA takes WARPS consecutive chunks per step and reserves list space for all of them
+  // with one atomic, so the list stays ascending within the CTA's span
+  for (int64_t c0 = (int64_t)blockIdx.x * WARPS; c0 < nchunks; c0 += (int64_t)gridDim.x * WARPS) {
+    const int64_t c = c0 + wib;
+    uint32_t u0 = 0, u1 = 0, u2 = 0, u3 = 0;
+    if (c < nchunks) {
+      const uint4 w4 = __ldg(vc + c * 32 + lane);
+      vn[c * 32 + lane] = w4;
+      u0 = ~w4.x;
+      u1 = ~w4.y;
+      u2 = ~w4.z;
+      u3 = ~w4.w;
+    }
     const int cnt = __popc(u0) + __popc(u1) + __popc(u2) + __popc(u3);
     const int total = warp_sum(cnt);
+    if (lane == 0) s_off[wib] = (unsigned long long)total;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long run = 0;
+      for (int i = 0; i < WARPS; ++i) {
+        const unsigned long long t = s_off[i];
+        s_off[i] = run;
+        run += t;
+      }
+      const unsigned long long base = run ? atomicAdd((unsigned long long*)&ctl->ulist_n, run) : 0ull;
+      for (int i = 0; i < WARPS; ++i) s_off[i] += base;
+    }
+    __syncthreads();
+    unsigned long long p = s_off[wib];
+    __syncthreads();  // s_off is rewritten in the next step
     if (total == 0) continue;
-    unsigned long long p = 0;
-    if (lane == 0) p = atomicAdd((unsigned long long*)&ctl->ulist_n, (unsigned long long)total);
-    p = __shfl_sync(FULL, p, 0);
     unsigned lanes = __ballot_sync(FULL, cnt != 0);
     while (lanes) {
       const int j = __ffs(lanes) - 1;
