@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--cpu-roots", type=int, default=1)
     ap.add_argument("--no-extras", action="store_true", help="skip plain/e2e/roofline passes")
     ap.add_argument("--trace-out", default="")
+    ap.add_argument("--bu-hub-first", action="store_true",
+                    help="degree-aware bottom-up (Alg. 3 probe order, min-id parents restored after the loop)")
     ap.add_argument("--launch-mode", default="graph", choices=["graph", "host"],
                     help="host: one launch per kernel (lets ncu see every kernel; slower)")
     ap.add_argument("--workload", default="et", choices=["et", "batch", "serve", "study"],
@@ -326,6 +328,8 @@ def main():
     build_s = time.time() - t0
     if a.launch_mode == "host":
         g.set_tuning(launch_mode=1)
+    if a.bu_hub_first:
+        g.set_tuning(bu_hub_first=1)
     st = g.stats()
     deg = g.degree()
     all_roots = graphgen.pick_roots(a.root_seed, n, a.roots * world, deg)

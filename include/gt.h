@@ -81,6 +81,10 @@ typedef struct gt_tuning {
                            summed degree * batch_alpha > core edges (default 14) */
   int32_t batch_beta;   /* gt_bfs_batch: back to top-down when frontier * batch_beta < core
                            vertices and shrinking (default 24) */
+  int32_t bu_hub_first; /* 1: degree-aware bottom-up (Alg. 3): each unvisited vertex first
+                           tests its highest-degree neighbour; a vertex found that way gets
+                           its min-id parent from one ascending pass after the level loop.
+                           Default 0 (measured slower; results are the same either way) */
 } gt_tuning;
 
 typedef struct gt_stats {

@@ -27,7 +27,7 @@ class gt_config(ctypes.Structure):
 class gt_tuning(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
         "alpha", "beta", "td_warp_min", "td_cta_min", "td_grid_min", "bu_thread_scan", "blocks_per_sm",
-        "force_direction", "launch_mode", "count_work", "time_kernels", "batch_alpha", "batch_beta")]
+        "force_direction", "launch_mode", "count_work", "time_kernels", "batch_alpha", "batch_beta", "bu_hub_first")]
 
 
 class gt_stats(ctypes.Structure):

@@ -37,6 +37,7 @@ struct BfsArgs {
   int32_t* queues;  // [2][NBINS][n]
   int32_t* ulist;
   const int4* pre;         // adjacency prefix records (null: none)
+  const int32_t* hub;      // highest-degree neighbours (degree-aware bottom-up; null: off)
   BfsCtl* ctl;
   int32_t td_warp_min;
   int32_t td_cta_min;
@@ -58,6 +59,7 @@ BfsArgs make_args(const View& v, const gt_tuning& t) {
   a.queues = v.queues;
   a.ulist = v.ulist;
   a.pre = v.pre;
+  a.hub = t.bu_hub_first ? v.hub : nullptr;
   a.ctl = v.ctl;
   a.td_warp_min = std::max(1, t.td_warp_min);
   a.td_cta_min = std::max(a.td_warp_min, t.td_cta_min);
@@ -517,6 +519,63 @@ __global__ void __launch_bounds__(BFS_THREADS) bfs_bu_gather(BfsArgs a) {
         p += __popc(m);
       }
     }
+  }
+}
+
+// Degree-aware bottom-up (Alg. 3), before the scan: every listed vertex tests its
+// highest-degree neighbour; one in the frontier settles the level, and the vertex leaves
+// the list with its parent left pending (HUB_PENDING): the first hit of this order is
+// not the smallest frontier neighbour, which bfs_hub_parents finds after the level loop.
+constexpr uint32_t HUB_PENDING = 0xFFFFFFFFu;
+
+__global__ void __launch_bounds__(BFS_THREADS) bfs_bu_hub(BfsArgs a) {
+  BfsCtl* ctl = a.ctl;
+  const uint32_t* __restrict__ vc = ctl->vcur ? a.vis1 : a.vis0;
+  uint32_t* vn = ctl->vcur ? a.vis0 : a.vis1;
+  const uint64_t hi = (uint64_t)(uint32_t)(ctl->level + 1) << 32;
+  const int64_t nu = ctl->ulist_n;
+  const int lane = threadIdx.x & 31;
+  int64_t nf = 0, mf = 0, examined = 0;
+  for (int64_t base = gtid() & ~(int64_t)31; base < nu; base += gthreads()) {
+    const int64_t i = base + lane;
+    const int32_t w = i < nu ? a.ulist[i] : -1;
+    bool fnd = false;
+    if (w >= 0) {
+      const int32_t h = a.hub[w];
+      if (h >= 0) {
+        ++examined;
+        fnd = (__ldg(&vc[h >> 5]) >> (h & 31)) & 1u;
+      }
+      if (fnd) {
+        a.state[w] = hi | HUB_PENDING;
+        a.ulist[i] = -1;  // the scan skips it
+        ++nf;
+        mf += a.row[w + 1] - a.row[w];
+      }
+    }
+    const unsigned peers = __match_any_sync(FULL, fnd ? (w >> 5) : -1);
+    const unsigned bits = __reduce_or_sync(peers, fnd ? (1u << (w & 31)) : 0u);
+    if (fnd && lane == __ffs(peers) - 1) atomicOr(&vn[w >> 5], bits);
+  }
+  block_commit(a, nf, mf, examined);
+}
+
+// Parents left pending by bfs_bu_hub: the first neighbour in ascending order one level up
+// (it exists: the highest-degree neighbour is one), i.e. the smallest frontier neighbour.
+__global__ void bfs_hub_parents(BfsArgs a) {
+  for (int64_t v = gtid(); v < a.n; v += gthreads()) {
+    const uint64_t st = a.state[v];
+    if (st == UNVISITED || (uint32_t)st != HUB_PENDING) continue;
+    const uint32_t lv = (uint32_t)(st >> 32);
+    uint32_t p = HUB_PENDING;
+    for (int64_t k = a.row[v]; k < a.row[v + 1]; ++k) {
+      const int32_t u = a.col[k];
+      if ((uint32_t)(a.state[u] >> 32) == lv - 1) {
+        p = (uint32_t)u;
+        break;
+      }
+    }
+    a.state[v] = ((uint64_t)lv << 32) | p;
   }
 }
 
@@ -1056,6 +1115,7 @@ void launch_step(int kind, const BfsArgs& a, int grid, cudaStream_t s) {
   }
   if (kind == 2 || kind == 4) bfs_mark<<<grid, BFS_THREADS, 0, s>>>(a);
   bfs_bu_gather<<<grid, BFS_THREADS, 0, s>>>(a);
+  if (a.hub) bfs_bu_hub<<<grid, BFS_THREADS, 0, s>>>(a);
   if (kind == 4) {
     if (a.pre)
       bfs_bu_scan<true, true><<<grid, BFS_THREADS, HASH_SMEM, s>>>(a);
@@ -1207,6 +1267,10 @@ int run_level_loop(gt_graph* g, View& v, int which, cudaStream_t s) {
 
 int run_bfs(gt_graph* g, View& v, bool et, int64_t root, int32_t* parent, int32_t* level, cudaStream_t s) {
   const gt_tuning& t = g->tuning;
+  if (t.bu_hub_first) {
+    const int rc0 = ensure_hub(g, v, s);
+    if (rc0 != GT_OK) return rc0;
+  }
   const BfsArgs a = make_args(v, t);
   const bool timed = t.time_kernels;
   if (timed && !g->phase_events[0])
@@ -1225,6 +1289,7 @@ int run_bfs(gt_graph* g, View& v, bool et, int64_t root, int32_t* parent, int32_
   rc = run_level_loop(g, v, et ? 0 : 1, s);
   if (rc != GT_OK) return rc;
   if (timed) cudaEventRecord(g->phase_events[2], s);
+  if (a.hub) bfs_hub_parents<<<grid_stream(g, v.n), 256, 0, s>>>(a);
   if (et) {
     const int go = grid_stream(g, g->n);
     const int vec = ((uintptr_t)parent % 16 == 0) && ((uintptr_t)level % 16 == 0);

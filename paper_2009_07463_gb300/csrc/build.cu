@@ -390,6 +390,34 @@ static __global__ void build_prefix(const int64_t* __restrict__ row, const int32
   }
 }
 
+// Highest-degree neighbour of every vertex of a view (ties: the smaller id, the first met
+// in the ascending row); -1 for an empty row. The probe order of the degree-aware bottom-up
+// step (Alg. 3).
+static __global__ void build_hub(const int64_t* __restrict__ row, const int32_t* __restrict__ col, int64_t n,
+                                 int32_t* __restrict__ hub) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    int32_t best = -1;
+    int64_t bd = -1;
+    for (int64_t k = row[v]; k < row[v + 1]; ++k) {
+      const int32_t u = col[k];
+      const int64_t d = row[u + 1] - row[u];
+      if (d > bd) {
+        bd = d;
+        best = u;
+      }
+    }
+    hub[v] = best;
+  }
+}
+
+int ensure_hub(gt_graph* g, View& v, cudaStream_t s) {
+  if (v.hub || v.n <= 0) return GT_OK;
+  int rc = device_malloc(g, (void**)&v.hub, sizeof(int32_t) * v.n);
+  if (rc) return rc;
+  build_hub<<<grid_for(g, v.n), BT, 0, s>>>(v.row, v.col, v.n, v.hub);
+  return cuda_fail(cudaGetLastError(), "hub neighbours");
+}
+
 int alloc_view_state(gt_graph* g, View& v, cudaStream_t s) {
   const int64_t n = v.n > 0 ? v.n : 1;
   v.nwords = (n + 31) / 32;
@@ -413,6 +441,7 @@ static void free_view(View& v) {
   cudaFree(v.ulist);
   cudaFree(v.ctl);
   cudaFree(v.pre);
+  cudaFree(v.hub);
   v = View{};
 }
 

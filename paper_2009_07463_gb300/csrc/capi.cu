@@ -232,6 +232,7 @@ GT_API void gt_tuning_default(gt_tuning* t) {
   t->force_direction = 0;
   t->launch_mode = 0;
   t->count_work = 0;
+  t->bu_hub_first = 0;
   t->time_kernels = 0;
   t->batch_alpha = 14;
   t->batch_beta = 24;
@@ -316,7 +317,7 @@ GT_API int gt_graph_set_tuning(gt_graph_t g, const gt_tuning* t) {
       t->bu_thread_scan < 0 || t->blocks_per_sm < 1 || t->blocks_per_sm > 32 || t->force_direction < 0 ||
       t->force_direction > 2 || t->launch_mode < 0 || t->launch_mode > 1 || t->time_kernels < 0 ||
       t->time_kernels > 1 || t->batch_alpha < 1 ||
-      t->batch_beta < 1) {
+      t->batch_beta < 1 || t->bu_hub_first < 0 || t->bu_hub_first > 1) {
     set_error("gt_graph_set_tuning: value out of range");
     return GT_EINVAL;
   }

@@ -71,6 +71,7 @@ struct View {
   // per vertex {degree, first three neighbours in ascending order (-1 past the degree)}:
   // one sequential 16-byte read answers most bottom-up probes (null: probe the CSR only)
   int4* pre = nullptr;
+  int32_t* hub = nullptr;  // per vertex its highest-degree neighbour (degree-aware bottom-up; built on first use)
   const int32_t* new2old = nullptr;  // view id -> vertex id (core view); null when ids agree
   BfsCtl* ctl = nullptr;
 };
@@ -162,6 +163,7 @@ int cuda_fail(cudaError_t e, const char* what);
 // build.cu
 int build_graph(gt_graph* g, const int64_t* edges, int64_t m, int64_t n, cudaStream_t s);
 int alloc_view_state(gt_graph* g, View& v, cudaStream_t s);
+int ensure_hub(gt_graph* g, View& v, cudaStream_t s);
 void free_graph(gt_graph* g);
 int device_malloc(gt_graph* g, void** p, size_t bytes);
 

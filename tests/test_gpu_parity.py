@@ -170,6 +170,32 @@ def test_direction_and_launch_mode_independence(torch_cuda):
                     assert_same(bfs_dev(torch, g, r, plain=True), w, what + " plain")
 
 
+def test_degree_aware_bottom_up(torch_cuda):
+    # Alg. 3 order (highest-degree neighbour first, min-id parents restored after the loop)
+    # gives the oracle's levels and parents, with the switch and with bottom-up forced, on
+    # the core and plain views, an R-MAT graph and the hand-made graphs (every root)
+    torch = torch_cuda
+    scale, n = 14, 1 << 14
+    e = graphgen.rmat_edges(scale, 16, seed=19)
+    og, g = build_pair(e, n)
+    roots = graphgen.pick_roots(6, n, 6, og.degree())
+    want = oracle_many(og, roots)
+    for force in (0, 2):
+        g.set_tuning(bu_hub_first=1, force_direction=force)
+        for r, w in zip(roots.tolist(), want):
+            assert_same(bfs_dev(torch, g, r), w, f"hub force={force} root {r}")
+            assert_same(bfs_dev(torch, g, r, plain=True), w, f"hub force={force} plain root {r}")
+    g.free()
+    for name in sorted(HAND):
+        pairs, nh = HAND[name]
+        og, g = build_pair(np.array(pairs, dtype=np.int64), nh, 0)
+        g.set_tuning(bu_hub_first=1, force_direction=2)
+        for r in range(nh):
+            assert_same(bfs_dev(torch, g, r), og.bfs(r), f"hub {name} root {r}")
+            assert_same(bfs_dev(torch, g, r, plain=True), og.bfs(r), f"hub {name} plain root {r}")
+        g.free()
+
+
 def test_trace_directions(torch_cuda):
     torch = torch_cuda
     n = 1 << 16
