@@ -56,6 +56,7 @@ def test_defaults_and_errors_without_gpu():
     L = gt.lib()
     t = gt.tuning_default()
     assert (t.alpha, t.beta, t.td_warp_min, t.launch_mode, t.batch_alpha) == (32, 256, 32, 0, 14)
+    assert (t.bu_thread_scan, t.bu_hub_first) == (24, 0)  # ascending bottom-up order by default
     assert L.gt_strerror(-1) == b"invalid argument"
     # argument checks fail before any device work
     h = ctypes.c_void_p()
