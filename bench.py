@@ -34,7 +34,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-E2E_CHUNK = 8  # roots per gt_bfs_roots call in the end-to-end pass
+E2E_CHUNK = 16  # roots per gt_bfs_roots call in the end-to-end pass
 HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e nominal bandwidth, reported beside the measured copy peak
 METRIC = "harmonic-mean GTEPS over 64 roots at R-MAT scale 26; served queries/s and p99"
 UNIT = "GTEPS"
