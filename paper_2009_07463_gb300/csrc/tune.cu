@@ -95,8 +95,9 @@ int autotune(gt_graph* g, int nsample, uint64_t seed, cudaStream_t s, gt_tuning*
     return cuda_fail(cudaEventElapsedTime(ms, e0, e1), "tune time");
   };
 
+  using Field = int32_t gt_tuning::*;
   struct Knob {
-    int32_t gt_tuning::*field;
+    Field field;
     std::vector<int32_t> values;
     bool batch;
   };
