@@ -75,6 +75,7 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-join-levels", type=int, default=-1,
                     help="level boundaries at which queries may join a running batched launch (-1: library default)")
+    ap.add_argument("--serve-streams", type=int, default=2, help="server streams (flights at once)")
     ap.add_argument("--serve-policies", default="adaptive,batched,single",
                     help="server dispatch policies to run on each arrival schedule (the first is the headline)")
     return ap.parse_args()
@@ -644,10 +645,10 @@ def run_batch_workload(a, rank, local):
     print(json.dumps(out), flush=True)
 
 
-def _serve_once(gt, graphs, bufs, RING, nq, gaps, gsel, roots, policy, join_levels=-1):
+def _serve_once(gt, graphs, bufs, RING, nq, gaps, gsel, roots, policy, join_levels=-1, streams=2):
     """One arrival schedule through a server with the given dispatch policy."""
     import threading
-    srv = gt.Server(hbm_budget_bytes=48 << 30, streams=2, max_batch_roots=128, window_us=100, policy=policy,
+    srv = gt.Server(hbm_budget_bytes=48 << 30, streams=streams, max_batch_roots=128, window_us=100, policy=policy,
                     join_levels=None if join_levels < 0 else join_levels)
     gids = [srv.add_graph(g) for g in graphs]
     slot_busy = [[None] * RING for _ in graphs]
@@ -730,7 +731,8 @@ def run_serve_workload(a, rank, local):
         for pol in [x for x in a.serve_policies.split(",") if x]:
             served[pol] = _serve_once(gt, graphs, bufs, RING, nq, gaps, gsel, roots,
                                       {"adaptive": gt.GT_SERVE_ADAPTIVE, "batched": gt.GT_SERVE_BATCHED,
-                                       "single": gt.GT_SERVE_SINGLE}[pol], a.serve_join_levels)
+                                       "single": gt.GT_SERVE_SINGLE}[pol], a.serve_join_levels,
+                                      a.serve_streams)
         # sequential single-root calls on the same schedule (one worker, FIFO)
         lat2 = []
         stream = torch.cuda.current_stream()
@@ -758,7 +760,7 @@ def run_serve_workload(a, rank, local):
            "unit": "queries/s", "p99_us": best["served"][head]["p99_us"], "policy": head, "n_gpus": 1, "higher_is_better": True,
            "dtype": "int32", "data": "synthetic",
            "config": {"workload": "serve: 12 resident graphs (rmat s18-25 ef16, uniform 2^20 deg 8/16/24/32), "
-                                  "Poisson arrivals", "hbm_budget_gib": 48, "streams": 2, "max_batch_roots": 128,
+                                  "Poisson arrivals", "hbm_budget_gib": 48, "streams": a.serve_streams, "max_batch_roots": 128,
                       "window_us": 100, "seconds_per_rate": a.serve_seconds},
            "rates": results}
     print(json.dumps(out), flush=True)
