@@ -163,7 +163,7 @@ GT_API int gt_bfs_plain(gt_graph_t g, int64_t root, int32_t* parent, int32_t* le
  * would, as rows of parent[i] / level[i]: device int32 [roots_per_graph[i]][n_i], row r
  * for root r. Roots are packed 64 to a lane word; the words of all graphs advance level
  * by level in one persistent cooperative launch that shares every adjacency read among
- * the word's roots. Per-graph lane-word storage (about 350 bytes per core vertex per 64
+ * the word's roots. Per-graph lane-word storage (about 420 bytes per core vertex per 64
  * roots) is allocated on first use and kept in the handle. At most 16384 roots per call.
  * All graphs must live on one device. Synchronises `stream`. GT_ETIMEOUT if a bounded
  * grid-barrier wait ran out, GT_ENOTSUP if a traversal is deeper than 65533 levels. */
