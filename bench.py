@@ -75,7 +75,7 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-join-levels", type=int, default=-1,
                     help="level boundaries at which queries may join a running batched launch (-1: library default)")
-    ap.add_argument("--serve-streams", type=int, default=2, help="server streams (flights at once)")
+    ap.add_argument("--serve-streams", type=int, default=4, help="server streams (flights at once)")
     ap.add_argument("--serve-policies", default="adaptive,batched,single",
                     help="server dispatch policies to run on each arrival schedule (the first is the headline)")
     return ap.parse_args()

@@ -208,7 +208,8 @@ GT_API int gt_count_traversed(const int64_t* edges, int64_t m, const int32_t* le
  * gt_bfs, gt_bfs_plain, gt_bfs_trace or gt_autotune: those share its traversal state. */
 typedef struct gt_serve_config {
   int64_t hbm_budget_bytes; /* graphs + batch storage admitted up to this (default 48 GiB) */
-  int32_t streams;          /* flights (batched or single-root) at once (default 2) */
+  int32_t streams;          /* flights at once, at most two of them batched launches, each on
+                               half of the SMs (default 4) */
   int32_t max_batch_roots;  /* roots per launch (default 256) */
   double window_us;         /* wait to fill lane words while other batches run (default 200) */
   int32_t policy;           /* GT_SERVE_ADAPTIVE (default), GT_SERVE_BATCHED or GT_SERVE_SINGLE */

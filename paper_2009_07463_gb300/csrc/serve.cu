@@ -245,6 +245,11 @@ bool grow_slots(gt_server* s, GraphEntry& ge) {
   return true;
 }
 
+// Batched launches at once: each takes 1/max_batched of the SMs (cooperative launches
+// need their CTAs resident together); the other streams run single-root flights, whose
+// kernels share the GPU. Two halves beat more, smaller launches at saturation.
+int max_batched(const gt_server* s) { return std::max(1, std::min<int>(2, (int)s->streams.size())); }
+
 // Picks the graph whose oldest pending query is oldest, among graphs without a running
 // single-root flight; -1 if none. Caller holds the lock.
 int oldest_graph(gt_server* s) {
@@ -265,10 +270,14 @@ void scheduler(gt_server* s) {
   cudaSetDevice(s->device);
   std::unique_lock<std::mutex> lk(s->mu);
   for (;;) {
-    int free_stream = -1, busy = 0;
+    int free_stream = -1, busy = 0, busy_batched = 0;
     for (size_t i = 0; i < s->flights.size(); ++i) {
-      if (s->flights[i]) ++busy;
-      else if (free_stream < 0) free_stream = (int)i;
+      if (s->flights[i]) {
+        ++busy;
+        busy_batched += s->flights[i]->single ? 0 : 1;
+      } else if (free_stream < 0) {
+        free_stream = (int)i;
+      }
     }
     if (s->stop && busy == 0) break;
     // lanes of running batched launches that have finished complete at once; pending
@@ -329,6 +338,10 @@ void scheduler(gt_server* s) {
                                (ge.est_single_us > 0 && ge.est_word_us > 0 && 64 * ge.est_single_us > ge.est_word_us);
     if (!single && busy > 0 && want < 64 && age < s->cfg.window_us && batching_pays) {
       s->cv_sched.wait_for(lk, std::chrono::microseconds((int64_t)std::max(1.0, s->cfg.window_us - age)));
+      continue;
+    }
+    if (!single && busy_batched >= max_batched(s)) {  // the batched share of the SMs is taken
+      s->cv_sched.wait_for(lk, std::chrono::microseconds(200));
       continue;
     }
     if (single) {
@@ -419,7 +432,7 @@ void scheduler(gt_server* s) {
     }
     cudaStream_t st = s->streams[free_stream];
     BatchCtx* ctx = &s->ctxs[free_stream];
-    const int share = std::max(1, s->sms / (int)s->streams.size());
+    const int share = std::max(1, s->sms / max_batched(s));
     // with free lanes and join_levels > 0 the launch takes roots through the stream's
     // mailbox, and reports there the lanes that end before the launch does
     f->capacity = s->cfg.join_levels > 0 ? std::min<int>(MAILBOX_CAP, words * 64 - (int)take) : 0;
@@ -476,7 +489,7 @@ GT_API void gt_serve_config_default(gt_serve_config* c) {
   if (!c) return;
   memset(c, 0, sizeof(*c));
   c->hbm_budget_bytes = (int64_t)48 << 30;
-  c->streams = 2;
+  c->streams = 4;  // two of them batched at most (max_batched)
   c->max_batch_roots = 256;
   c->window_us = 200.0;
   c->policy = GT_SERVE_ADAPTIVE;

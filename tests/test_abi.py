@@ -68,7 +68,7 @@ def test_defaults_and_errors_without_gpu():
     # server configuration is checked before the server touches a device
     c = gt.gt_serve_config()
     L.gt_serve_config_default(ctypes.byref(c))
-    assert (c.streams, c.max_batch_roots, c.policy, c.join_levels) == (2, 256, gt.GT_SERVE_ADAPTIVE, 0)
+    assert (c.streams, c.max_batch_roots, c.policy, c.join_levels) == (4, 256, gt.GT_SERVE_ADAPTIVE, 0)
     c.policy = 3
     assert L.gt_serve_create(ctypes.byref(c), ctypes.byref(h)) == gt.GT_EINVAL
     c.policy = gt.GT_SERVE_ADAPTIVE
