@@ -9,8 +9,8 @@
 // single-root flight at a time (the traversal state is the graph's own). A batched
 // launch is dispatched at once when the GPU is idle; otherwise, if batching pays on that
 // graph, the scheduler waits up to `window_us` to fill lane words. Flights on different
-// streams overlap on the device (a cooperative batched launch takes 1/streams of the
-// SMs). Graphs are admitted against an HBM budget
+// streams overlap on the device; at most two are batched launches, each cooperative on
+// half of the SMs. Graphs are admitted against an HBM budget
 // (graph storage + one lane word of batch storage); more lane-word storage is taken
 // while the budget allows. Completion is signalled by a host callback on the stream,
 // which stamps every query's latency (submit -> results in the caller's buffers). With
