@@ -8,6 +8,10 @@
 - BFS invariants on R-MAT graphs: level[root] = 0, levels across an edge differ by <= 1,
   every parent is a neighbour one level up and the smallest such.
 - CSR against a set-of-pairs construction with duplicates and self-loops planted.
+- TEPS numerator (traversed_tuples) against counts fixed by hand on a tuple list with
+  duplicates, self-loops on reached and unreached vertices and a second component.
+  Checked by hand: skipping self-loops, testing level > 0, or stopping one tuple early in
+  or_traversed_tuples each fails these tests.
 """
 import itertools
 
@@ -211,3 +215,42 @@ def test_rmat_invariants(scale):
         # the TEPS numerator counts the tuples inside the root's component
         cnt = traversed_tuples(e, lv)
         assert cnt == int(((lv[e[:, 0]] >= 0) & (lv[e[:, 1]] >= 0)).sum())
+
+
+# Hand-built tuple list for the TEPS numerator (Graph500 convention, Sec. 6.1: every input
+# tuple whose two ends are reached counts once, duplicates and self-loops included).
+HAND_TUPLES = [
+    (0, 1),  # 0
+    (1, 0),  # 1  duplicate of 0, ends flipped
+    (1, 2),  # 2
+    (2, 2),  # 3  self-loop on a vertex reached from 0
+    (0, 1),  # 4  duplicate of 0, same order
+    (3, 4),  # 5  second component
+    (5, 5),  # 6  self-loop on a vertex with no other edge
+    (4, 4),  # 7  self-loop in the second component
+    (2, 0),  # 8
+    (6, 3),  # 9  second component, last tuple
+]
+
+
+@pytest.mark.parametrize("root,want", [(0, 6), (1, 6), (3, 3), (6, 3), (5, 1)])
+def test_traversed_tuples_hand_counts(root, want):
+    """Counts fixed by hand from the list above: root 0 or 1 reaches {0, 1, 2} (tuples 0-4
+    and 8: the two duplicates and the self-loop count); root 3 or 6 reaches {3, 4, 6}
+    (tuples 5, 7, 9); root 5 reaches only itself, and its self-loop counts. Dropping
+    self-loops, merging duplicates, skipping the root (level 0) or the last tuple each
+    change one of these numbers."""
+    e = np.array(HAND_TUPLES, dtype=np.int64)
+    g = OracleGraph(e, 7)
+    lv, _ = g.bfs(root)
+    assert traversed_tuples(e, lv) == want
+
+
+def test_traversed_tuples_given_levels():
+    """The count depends only on which ends have level >= 0, whatever the levels are."""
+    e = np.array(HAND_TUPLES, dtype=np.int64)
+    assert traversed_tuples(e, np.full(7, -1, np.int32)) == 0
+    assert traversed_tuples(e, np.array([-1, -1, 7, -1, -1, -1, -1], np.int32)) == 1   # tuple 3
+    assert traversed_tuples(e, np.array([-1, -1, -1, 0, 2, -1, -1], np.int32)) == 2    # tuples 5, 7
+    assert traversed_tuples(e, np.array([-1, -1, -1, -1, -1, -1, 0], np.int32)) == 0   # 6's tuple needs 3
+    assert traversed_tuples(e, np.zeros(7, np.int32)) == 10
