@@ -264,10 +264,13 @@ GT_API int gt_serve_destroy(gt_server_t s);
  * one file-scope device array of about 12 MB, reserved on every device that loads the
  * library until the process exits, so n is limited to 262,144 vertices (GT_EINVAL above).
  * No cudaMalloc, cudaFree or allocating library routine is called. The first call on a
- * device looks up the array's device address; make that first call before any stream
- * capture. Every call uses the same array, so calls that overlap on the GPU (other
- * streams, other threads) race and must be serialised by the caller. Synchronises
- * `stream` once per level. */
+ * device looks up the array's device address (cudaGetSymbolAddress) and caches it. Every
+ * call uses the same array, so calls that overlap on the GPU (other streams, other
+ * threads) race and must be serialised by the caller. The call reads nnz and, once per
+ * level, the control block back to the host and synchronises `stream` each time, so it
+ * returns with the results in place and cannot be called on a stream that is being
+ * captured. GT_EINVAL for a null pointer, n < 1 or above the limit, a root outside
+ * [0, n), or a buffer that is not memory of the current device. */
 GT_API int gt_bfs_csr_noalloc(const int64_t* row, const int32_t* col, int64_t n, int64_t root, int32_t* parent,
                               int32_t* level, void* stream);
 

@@ -126,20 +126,25 @@ def _ptr(x) -> int:
     raise TypeError(f"cannot take a pointer of {type(x)}")
 
 
-def _out(x, count: int, what: str) -> int:
-    """Pointer of an int32 output buffer, after checking that an array or tensor holds at
-    least `count` contiguous int32 entries (raw integer pointers are taken as given)."""
+def _buf(x, count: int, what: str, dtype: str = "int32") -> int:
+    """Pointer of a buffer, after checking that an array or tensor holds at least `count`
+    contiguous entries of `dtype` (raw integer pointers are taken as given)."""
     if x is None or isinstance(x, int):
         return _ptr(x)
     if isinstance(x, np.ndarray):
-        ok = x.dtype == np.int32 and x.flags.c_contiguous and x.size >= count
+        ok = x.dtype == np.dtype(dtype) and x.flags.c_contiguous and x.size >= count
     elif hasattr(x, "numel"):
-        ok = str(x.dtype) == "torch.int32" and x.is_contiguous() and x.numel() >= count
+        ok = str(x.dtype) == f"torch.{dtype}" and x.is_contiguous() and x.numel() >= count
     else:
         raise TypeError(f"{what}: cannot take a pointer of {type(x)}")
     if not ok:
-        raise ValueError(f"{what}: need a contiguous int32 buffer of at least {count} entries")
+        raise ValueError(f"{what}: need a contiguous {dtype} buffer of at least {count} entries")
     return _ptr(x)
+
+
+def _out(x, count: int, what: str) -> int:
+    """Pointer of an int32 output buffer of at least `count` entries (see _buf)."""
+    return _buf(x, count, what)
 
 
 def _stream(s) -> int:
@@ -401,8 +406,17 @@ class Server:
 
 def gt_bfs_csr_noalloc(row, col, n: int, root: int, parent, level, stream=None) -> None:
     """Plain BFS on a caller's device CSR without any device allocation (fixed scratch;
-    n <= 262,144); same results as gt_bfs_plain."""
-    _check(lib().gt_bfs_csr_noalloc(_ptr(row), _ptr(col), int(n), int(root), _out(parent, n, "parent"),
+    n <= 262,144); same results as gt_bfs_plain. row: int64[n + 1], col: int32[row[n]]
+    (tensors are checked for dtype, contiguity and length before the call; the length of
+    col against row[n] costs one 8-byte read of row)."""
+    n = int(n)
+    rp = _buf(row, n + 1, "row", "int64")
+    cp = _buf(col, 0, "col", "int32")
+    if hasattr(row, "numel") and hasattr(col, "numel") and 0 < n < row.numel():
+        nnz = int(row[n].item())
+        if nnz < 0 or col.numel() < nnz:
+            raise ValueError(f"col: row[n] = {nnz} entries, but col holds {col.numel()}")
+    _check(lib().gt_bfs_csr_noalloc(rp, cp, n, int(root), _out(parent, n, "parent"),
                                     _out(level, n, "level"), _stream(stream)), "gt_bfs_csr_noalloc")
 
 

@@ -1368,13 +1368,15 @@ int noalloc_scratch(void** out) {
   return GT_OK;
 }
 
-bool on_device(const void* p) {
+// True for memory of device `dev` (device or managed); memory of another GPU is refused,
+// since the kernels would reach it without peer access.
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes at{};
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
 }
 
 }  // namespace
@@ -1392,16 +1394,17 @@ extern "C" GT_API int gt_bfs_csr_noalloc(const int64_t* row, const int32_t* col,
               std::to_string(NOALLOC_MAX_N) + " vertices");
     return GT_EINVAL;
   }
-  if (!on_device(row) || !on_device(col) || !on_device(parent) || !on_device(level)) {
-    set_error("gt_bfs_csr_noalloc: row, col, parent and level must be device memory");
+  int dev = 0, sms = 1;
+  int rc = cuda_fail(cudaGetDevice(&dev), "cudaGetDevice");
+  if (rc) return rc;
+  if (!on_device(row, dev) || !on_device(col, dev) || !on_device(parent, dev) || !on_device(level, dev)) {
+    set_error("gt_bfs_csr_noalloc: row, col, parent and level must be memory of the current device");
     return GT_EINVAL;
   }
   cudaStream_t s = (cudaStream_t)stream;
   void* base = nullptr;
-  int rc = noalloc_scratch(&base);
+  rc = noalloc_scratch(&base);
   if (rc) return rc;
-  int dev = 0, sms = 1;
-  cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int64_t nnz = 0;
   rc = cuda_fail(cudaMemcpyAsync(&nnz, row + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s), "read nnz");
@@ -1443,10 +1446,16 @@ extern "C" GT_API int gt_bfs_csr_noalloc(const int64_t* row, const int32_t* col,
     if (!rc) rc = cuda_fail(cudaStreamSynchronize(s), "level sync");
     if (rc) return rc;
     if (h.done) break;
+    // step kinds 0-3 only: kind 4 (frontier set in shared memory) needs the kernel
+    // attribute that prepare_kernels sets, which this path leaves alone
     launch_step(h.dir == DIR_TD ? (h.need_queue ? 3 : 0) : (h.need_mark ? 2 : 1), a, grid, s);
     bfs_decide<<<1, 1, 0, s>>>(a, 0, 0, 0);
     rc = cuda_fail(cudaGetLastError(), "level launch");
     if (rc) return rc;
+  }
+  if (!h.done) {  // a BFS has at most n levels; a loop that ran past them found an inconsistency
+    set_error("gt_bfs_csr_noalloc: level loop passed n + 2 steps without finishing");
+    return GT_EDEVICE;
   }
   plain_output<<<std::max(1, (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8)), 256, 0, s>>>(
       v.state, v.n, parent, level);
