@@ -244,8 +244,9 @@ def traffic_from_profiles(kernel: str) -> float | None:
 def launches_of(trace: list[dict]) -> int:
     """Kernels one gt_bfs launches: reset, start, per level the step kernels + decide, the
     anchor gather, output and the root-walk fix-up (resolve passes are absent at MH = 0 but
-    for K2 tops). Step kernels: top-down 1; bottom-up 2 (gather, scan), plus a mark after a
-    top-down step."""
+    for K2 tops). Step kernels: top-down 1, plus a queue rebuild after a bottom-up step;
+    bottom-up over the gathered list 2 (gather, scan), streaming bottom-up 1, each plus a
+    mark after a top-down step."""
     k = 5
     if not trace:
         return k + 2
@@ -253,9 +254,9 @@ def launches_of(trace: list[dict]) -> int:
     for t in trace:
         k += 1  # decide
         if t["direction"] == "td":
-            k += 1
+            k += 2 if prev == "bu" else 1
         else:
-            k += 3 if prev == "td" else 2
+            k += (1 if t.get("stream") else 2) + (1 if prev == "td" else 0)
         prev = t["direction"]
     return k
 

@@ -269,7 +269,8 @@ class Graph:
         out = []
         for i in range(min(nl.value, cap)):
             t = arr[i]
-            out.append({"level": t.level, "direction": "bu" if t.direction else "td", "frontier": t.frontier,
+            out.append({"level": t.level, "direction": "bu" if t.direction else "td", "stream": t.direction == 2,
+                        "frontier": t.frontier,
                         "frontier_edges": t.frontier_edges, "unvisited_edges": t.unvisited_edges,
                         "discovered": t.discovered, "examined": t.examined, "step_ms": t.step_ms})
         return out

@@ -180,8 +180,9 @@ __device__ __forceinline__ void td_visit_k(const BfsArgs& a, const uint32_t* vis
 
 // Adds per-thread counts into the control block with one atomic per CTA and counter.
 // Every thread of the CTA must call.
+template <int NW = WARPS>
 __device__ __forceinline__ void block_commit(const BfsArgs& a, int64_t n_found, int64_t m_found, int64_t examined) {
-  __shared__ int64_t red[3][WARPS];
+  __shared__ int64_t red[3][NW];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   n_found = warp_sum(n_found);
   m_found = warp_sum(m_found);
@@ -194,7 +195,7 @@ __device__ __forceinline__ void block_commit(const BfsArgs& a, int64_t n_found, 
   __syncthreads();
   if (threadIdx.x == 0) {
     int64_t x = 0, y = 0, z = 0;
-    for (int i = 0; i < WARPS; ++i) {
+    for (int i = 0; i < NW; ++i) {
       x += red[0][i];
       y += red[1][i];
       z += red[2][i];
@@ -804,6 +805,144 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) bfs_bu_scan(BfsArgs a) {
   block_commit(a, nf, mf, examined);
 }
 
+// Streaming bottom-up step, for a level at which most vertices are still unvisited (the
+// dense middle of the traversal). Instead of gathering the unvisited vertices into a list
+// and reading their records through it, each warp takes 32 x BU_V consecutive vertices
+// (BU_V bitmap words) and loads their visited words and prefix records together: the
+// records of consecutive vertices are consecutive, so one 512-byte coalesced load per
+// word, with no list in between. Unvisited vertices then go on exactly as in the scan
+// above (record probes, lane continuation, whole-warp continuation for long rows). The
+// warp owns its words of the next bitmap and writes each one whole (visited bits | bits
+// found), so neither the gather pass's copy nor per-word atomics are needed.
+__global__ void __launch_bounds__(BFS_THREADS, 4) bfs_bu_stream(BfsArgs a) {
+  BfsCtl* ctl = a.ctl;
+  const uint32_t* __restrict__ vc = ctl->vcur ? a.vis1 : a.vis0;
+  uint32_t* vn = ctl->vcur ? a.vis0 : a.vis1;
+  const uint64_t hi = (uint64_t)(uint32_t)(ctl->level + 1) << 32;
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = gtid() >> 5, nw = gthreads() >> 5;
+  const int alone = max(a.bu_scan - 3, 0);  // CSR probes per lane and vertex after the record
+  int64_t nf = 0, mf = 0, examined = 0;
+  for (int64_t w0 = gw * BU_V; w0 < a.nwords; w0 += nw * BU_V) {
+    uint32_t vw[BU_V];
+    int32_t w[BU_V], par[BU_V], d[BU_V];
+    int64_t s[BU_V], e[BU_V];
+    int4 r[BU_V];
+#pragma unroll
+    for (int j = 0; j < BU_V; ++j) {
+      vw[j] = __ldg(&vc[w0 + j]);
+      const int64_t v = (w0 + j) * 32 + lane;
+      r[j] = v < a.n ? __ldg(&a.pre[v]) : make_int4(0, -1, -1, -1);
+    }
+#pragma unroll
+    for (int j = 0; j < BU_V; ++j) {
+      const int64_t v = (w0 + j) * 32 + lane;
+      w[j] = (v < a.n && !((vw[j] >> lane) & 1u)) ? (int32_t)v : -1;  // padding bits are set
+      if (w[j] < 0) r[j] = make_int4(0, -1, -1, -1);
+    }
+    uint32_t b0[BU_V], b1[BU_V], b2[BU_V];
+#pragma unroll
+    for (int j = 0; j < BU_V; ++j) {
+      b0[j] = r[j].y >= 0 ? __ldg(&vc[r[j].y >> 5]) : 0u;
+      b1[j] = r[j].z >= 0 ? __ldg(&vc[r[j].z >> 5]) : 0u;
+      b2[j] = r[j].w >= 0 ? __ldg(&vc[r[j].w >> 5]) : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < BU_V; ++j) {
+      const bool h0 = r[j].y >= 0 && ((b0[j] >> (r[j].y & 31)) & 1u);
+      const bool h1 = r[j].z >= 0 && ((b1[j] >> (r[j].z & 31)) & 1u);
+      const bool h2 = r[j].w >= 0 && ((b2[j] >> (r[j].w & 31)) & 1u);
+      par[j] = h0 ? r[j].y : h1 ? r[j].z : h2 ? r[j].w : -1;
+      d[j] = r[j].x;
+      examined += h0 ? 1 : h1 ? 2 : h2 ? 3 : min(r[j].x, 3);
+      s[j] = 0;
+      e[j] = 0;
+      if (w[j] >= 0 && par[j] < 0 && d[j] > 3) {
+        s[j] = a.row[w[j]] + 3;
+        e[j] = s[j] - 3 + d[j];
+      }
+    }
+    int64_t nx[BU_V];
+#pragma unroll
+    for (int j = 0; j < BU_V; ++j) nx[j] = s[j];
+    for (int rd = 0; rd < alone; ++rd) {
+      int32_t u[BU_V];
+      bool any = false;
+#pragma unroll
+      for (int j = 0; j < BU_V; ++j) {
+        u[j] = -1;
+        if (par[j] < 0 && nx[j] < e[j] && nx[j] - s[j] < alone) {
+          u[j] = a.col[nx[j]];
+          any = true;
+        }
+      }
+      if (!any) break;
+      uint32_t pw[BU_V];
+#pragma unroll
+      for (int j = 0; j < BU_V; ++j) pw[j] = u[j] >= 0 ? __ldg(&vc[u[j] >> 5]) : 0u;
+#pragma unroll
+      for (int j = 0; j < BU_V; ++j) {
+        if (u[j] >= 0) {
+          ++nx[j];
+          if ((pw[j] >> (u[j] & 31)) & 1u) par[j] = u[j];
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < BU_V; ++j) examined += nx[j] - s[j];
+#pragma unroll
+    for (int j = 0; j < BU_V; ++j) {
+      bool fj = par[j] >= 0;
+      if (fj) {
+        a.state[w[j]] = hi | (uint32_t)par[j];
+        ++nf;
+        mf += d[j];
+      }
+      const int64_t lim = min(e[j], s[j] + (int64_t)alone);  // where this lane's own probes stopped
+      unsigned lm = __ballot_sync(FULL, w[j] >= 0 && !fj && lim < e[j]);
+      while (lm) {
+        const int src = __ffs(lm) - 1;
+        lm &= lm - 1;
+        const int32_t w2 = __shfl_sync(FULL, w[j], src);
+        const int64_t s2 = __shfl_sync(FULL, lim, src), e2 = __shfl_sync(FULL, e[j], src);
+        const int32_t d2 = __shfl_sync(FULL, d[j], src);
+        int32_t par2 = -1;
+        for (int64_t c0 = s2; c0 < e2 && par2 < 0; c0 += 32 * CW) {
+          int32_t uu[CW];
+          bool hh[CW];
+#pragma unroll
+          for (int t = 0; t < CW; ++t) {
+            const int64_t k2 = c0 + 32 * t + lane;
+            uu[t] = k2 < e2 ? a.col[k2] : -1;
+          }
+#pragma unroll
+          for (int t = 0; t < CW; ++t) hh[t] = uu[t] >= 0 && visited_bit(vc, uu[t]);
+#pragma unroll
+          for (int t = 0; t < CW; ++t) {
+            const unsigned hm = __ballot_sync(FULL, hh[t]);
+            if (par2 < 0 && hm) {
+              par2 = __shfl_sync(FULL, uu[t], __ffs(hm) - 1);
+              if (lane == 0) examined += 32 * t + __ffs(hm);
+            }
+          }
+          if (par2 < 0 && lane == 0) examined += min((int64_t)(32 * CW), e2 - c0);
+        }
+        if (par2 >= 0) {
+          if (lane == 0) {
+            a.state[w2] = hi | (uint32_t)par2;
+            ++nf;
+            mf += d2;
+          }
+          if (lane == src) fj = true;
+        }
+      }
+      const unsigned fb = __ballot_sync(FULL, fj);
+      if (lane == j) vn[w0 + j] = vw[j] | fb;
+    }
+  }
+  block_commit(a, nf, mf, examined);
+}
+
 // ---- level control -----------------------------------------------------------------
 // After each step: record the trace, swap queue sets (and bitmaps after bottom-up), and
 // pick the next direction by the frontier-size rule of Beamer et al. (the paper's
@@ -820,7 +959,7 @@ __global__ void bfs_decide(BfsArgs a, cudaGraphConditionalHandle h_loop, cudaGra
     if (c->nlevels < MAX_TRACE) {
       gt_level_info& t = c->trace[c->nlevels];
       t.level = L;
-      t.direction = dir;
+      t.direction = (dir == DIR_BU && c->bu_stream) ? 2 : dir;
       t.frontier = c->n_f;
       t.frontier_edges = c->m_f;
       t.unvisited_edges = c->m_u;
@@ -859,6 +998,10 @@ __global__ void bfs_decide(BfsArgs a, cudaGraphConditionalHandle h_loop, cudaGra
     c->need_mark = (dir == DIR_TD && nd == DIR_BU);
     c->need_queue = (dir == DIR_BU && nd == DIR_TD);
     c->bu_hash = c->need_mark && nn <= HASH_CAP;
+    c->n_visited += nn;
+    // stream when more than half of the vertices are unvisited and records exist (the
+    // degree-aware option works on the gathered list)
+    c->bu_stream = a.pre && !a.hub && (a.n - c->n_visited) * 2 > a.n;
     c->dir = nd;
   }
   if (use_handles) {
@@ -868,10 +1011,12 @@ __global__ void bfs_decide(BfsArgs a, cudaGraphConditionalHandle h_loop, cudaGra
 }
 
 // Which step kernels run next: 0 top-down, 1 bottom-up, 2 mark + bottom-up,
-// 3 queue rebuild + top-down, 4 mark + bottom-up probing a shared-memory frontier set.
+// 3 queue rebuild + top-down, 4 mark + bottom-up probing a shared-memory frontier set,
+// 5 streaming bottom-up, 6 mark + streaming bottom-up.
 __device__ __forceinline__ unsigned step_kind(const BfsCtl* c) {
   if (c->dir == DIR_TD) return c->need_queue ? 3u : 0u;
-  return c->need_mark ? (c->bu_hash ? 4u : 2u) : 1u;
+  if (c->need_mark) return c->bu_hash ? 4u : (c->bu_stream ? 6u : 2u);
+  return c->bu_stream ? 5u : 1u;
 }
 
 
@@ -909,6 +1054,7 @@ __device__ void ctl_begin(const BfsArgs& a, int32_t start, int32_t start_level, 
   c->ulist_n = 0;
   c->need_queue = 0;
   c->bu_hash = 0;
+  c->bu_stream = 0;
   c->alpha = alpha;
   c->beta = beta;
   c->force = force;
@@ -918,6 +1064,7 @@ __device__ void ctl_begin(const BfsArgs& a, int32_t start, int32_t start_level, 
   c->prev_n_f = 0;
   c->need_mark = 0;
   c->dir = force == 2 ? DIR_BU : DIR_TD;
+  c->n_visited = 0;
   if (start < 0) {
     c->done = 1;
     c->n_f = 0;
@@ -926,6 +1073,7 @@ __device__ void ctl_begin(const BfsArgs& a, int32_t start, int32_t start_level, 
     return;
   }
   c->done = 0;
+  c->n_visited = 1;
   const int64_t d = a.row[start + 1] - a.row[start];
   a.state[start] = ((uint64_t)(uint32_t)start_level << 32) | (uint32_t)start;
   a.vis0[start >> 5] |= 1u << (start & 31);
@@ -1089,7 +1237,7 @@ int grid_stream(const gt_graph* g, int64_t work) {
   return (int)std::max<int64_t>(1, std::min(want, cap));
 }
 
-constexpr int NKINDS = 5;
+constexpr int NKINDS = 7;
 constexpr size_t HASH_SMEM = sizeof(int32_t) * HASH_SLOTS;
 
 // Lets the shared-memory-set variant of the scan take its 64 KB of dynamic shared memory.
@@ -1106,14 +1254,18 @@ int prepare_kernels() {
 
 // The step kernels of one level: 0 top-down, 1 bottom-up (gather + scan), 2 mark +
 // bottom-up, 3 queue rebuild + top-down, 4 mark + bottom-up with the frontier set in
-// shared memory.
+// shared memory, 5 streaming bottom-up, 6 mark + streaming bottom-up.
 void launch_step(int kind, const BfsArgs& a, int grid, cudaStream_t s) {
   if (kind == 3) bfs_queue_from_bitmap<<<grid, BFS_THREADS, 0, s>>>(a);
   if (kind == 0 || kind == 3) {
     bfs_td<<<grid, BFS_THREADS, 0, s>>>(a);
     return;
   }
-  if (kind == 2 || kind == 4) bfs_mark<<<grid, BFS_THREADS, 0, s>>>(a);
+  if (kind == 2 || kind == 4 || kind == 6) bfs_mark<<<grid, BFS_THREADS, 0, s>>>(a);
+  if (kind == 5 || kind == 6) {
+    bfs_bu_stream<<<grid, BFS_THREADS, 0, s>>>(a);
+    return;
+  }
   bfs_bu_gather<<<grid, BFS_THREADS, 0, s>>>(a);
   if (a.hub) bfs_bu_hub<<<grid, BFS_THREADS, 0, s>>>(a);
   if (kind == 4) {
@@ -1129,9 +1281,10 @@ void launch_step(int kind, const BfsArgs& a, int grid, cudaStream_t s) {
   }
 }
 
-unsigned host_step_kind(int dir, int need_mark, int need_queue, int bu_hash) {
+unsigned host_step_kind(int dir, int need_mark, int need_queue, int bu_hash, int bu_stream) {
   if (dir == DIR_TD) return need_queue ? 3u : 0u;
-  return need_mark ? (bu_hash ? 4u : 2u) : 1u;
+  if (need_mark) return bu_hash ? 4u : (bu_stream ? 6u : 2u);
+  return bu_stream ? 5u : 1u;
 }
 
 // Builds the CUDA graph of the level loop for one view:
@@ -1221,7 +1374,7 @@ int run_level_loop(gt_graph* g, View& v, int which, cudaStream_t s) {
   const BfsArgs a = make_args(v, t);
   const int grid = g->launch.grid;
   struct Head {
-    int32_t level, dir, done, cur, vcur, need_mark, need_queue, bu_hash;
+    int32_t level, dir, done, cur, vcur, need_mark, need_queue, bu_hash, bu_stream;
   } h{};
   const cudaGraphConditionalHandle none = 0;
   int timed_steps = 0;
@@ -1243,7 +1396,7 @@ int run_level_loop(gt_graph* g, View& v, int which, cudaStream_t s) {
       }
       cudaEventRecord(g->step_events[2 * guard], s);
     }
-    launch_step((int)host_step_kind(h.dir, h.need_mark, h.need_queue, h.bu_hash), a, grid, s);
+    launch_step((int)host_step_kind(h.dir, h.need_mark, h.need_queue, h.bu_hash, h.bu_stream), a, grid, s);
     if (timed) {
       cudaEventRecord(g->step_events[2 * guard + 1], s);
       ++timed_steps;

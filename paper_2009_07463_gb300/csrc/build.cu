@@ -367,6 +367,10 @@ int bits_for(int64_t n) {
 
 }  // namespace
 
+// Column arrays are allocated in whole 16-byte pieces (the entries past nnz are never
+// used), so a kernel may read them as aligned vectors.
+int64_t col_alloc(int64_t nnz) { return (std::max<int64_t>(nnz, 1) + 3) / 4 * 4; }
+
 int device_malloc(gt_graph* g, void** p, size_t bytes) {
   if (bytes == 0) bytes = 16;
   cudaError_t e = cudaMalloc(p, bytes);
@@ -585,12 +589,12 @@ int build_graph(gt_graph* g, const int64_t* edges, int64_t m, int64_t n, cudaStr
       set_error("gt_graph_build: a tuple has a vertex id outside [0, n)");
       return GT_EINVAL;
     }
-    TRY(device_malloc(g, (void**)&g->col, sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
+    TRY(device_malloc(g, (void**)&g->col, sizeof(int32_t) * col_alloc(nnz)));
     uniq_write<<<(unsigned)nt, UT, 0, s>>>(keys, K, sent, b, tileoff, g->col, g->deg);
     TRYC(cudaGetLastError(), "uniq_write");
     // keys are freed with the temporaries
   } else {
-    TRY(device_malloc(g, (void**)&g->col, sizeof(int32_t)));
+    TRY(device_malloc(g, (void**)&g->col, sizeof(int32_t) * col_alloc(0)));
   }
   g->nnz = nnz;
   TRY(scan_i32_to_i64(g->deg, g->row, n, s, d_scan, scan_bytes));
@@ -662,7 +666,7 @@ int build_graph(gt_graph* g, const int64_t* edges, int64_t m, int64_t n, cudaStr
   TRY(scan_i32_to_i64(cdeg, cv.row, nc, s, d_scan, scan_bytes));
   TRYC(cudaMemcpyAsync(&cv.nnz, cv.row + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s), "readback");
   TRYC(cudaStreamSynchronize(s), "sync");
-  TRY(device_malloc(g, (void**)&cv.col, sizeof(int32_t) * std::max<int64_t>(cv.nnz, 1)));
+  TRY(device_malloc(g, (void**)&cv.col, sizeof(int32_t) * col_alloc(cv.nnz)));
   if (nc > 0) core_fill<<<gw, BT, 0, s>>>(g->row, g->col, is_core, g->new2old, g->old2core, nc, cv.row, cv.col);
   TRYC(cudaGetLastError(), "core csr");
 

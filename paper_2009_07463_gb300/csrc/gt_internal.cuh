@@ -38,7 +38,9 @@ struct BfsCtl {
   int32_t need_mark;  // 1: set visited bits of the current queue before a bottom-up step
   int32_t need_queue; // 1: rebuild the current queue from the bitmaps before a top-down step
   int32_t bu_hash;    // 1: the bottom-up step may probe a shared-memory copy of the frontier
+  int32_t bu_stream;  // 1: the bottom-up step streams all vertices (most are unvisited)
   int32_t nlevels;    // steps taken
+  int64_t n_visited;  // vertices visited so far
   int64_t n_f;        // current frontier vertices
   int64_t m_f;        // their summed degree
   int64_t prev_n_f;

@@ -21,9 +21,12 @@ def test_byte_models_follow_the_per_unit_figures():
 
 def test_launch_count_per_traversal():
     # reset, start, anchors, output, fixup + per level one decide and the step kernels
-    # (top-down 1; bottom-up gather + scan, plus a mark after top-down)
+    # (top-down 1, plus a queue rebuild after bottom-up; bottom-up gather + scan, or one
+    # streaming kernel, plus a mark after top-down)
     trace = [{"direction": "td"}, {"direction": "bu"}, {"direction": "bu"}, {"direction": "td"}]
-    assert bench.launches_of(trace) == 5 + 4 + 1 + 3 + 2 + 1
+    assert bench.launches_of(trace) == 5 + 4 + 1 + 3 + 2 + 2
+    trace = [{"direction": "td"}, {"direction": "bu", "stream": True}, {"direction": "bu", "stream": False}]
+    assert bench.launches_of(trace) == 5 + 3 + 1 + 2 + 2
 
 
 def test_harmonic_mean_ignores_non_positive():

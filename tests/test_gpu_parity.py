@@ -207,6 +207,10 @@ def test_trace_directions(torch_cuda):
     tr = g.trace()
     assert tr and tr[0]["frontier"] == 1
     assert {t["direction"] for t in tr} == {"td", "bu"}  # the switch does fire on R-MAT
+    # bottom-up levels stream over all vertices while most are unvisited, then scan the
+    # gathered list (both forms are in every oracle comparison of this module)
+    bu = [t for t in tr if t["direction"] == "bu"]
+    assert bu[0]["stream"] and not bu[-1]["stream"]
     assert all(t["examined"] >= 0 for t in tr)
     # plain BFS on the whole graph: every reached vertex but the root is discovered on
     # exactly one traced level, and the loop stops once no unvisited edge is left
