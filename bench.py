@@ -54,7 +54,8 @@ def parse():
     ap.add_argument("--mh", type=int, default=0)
     ap.add_argument("--cpu-baseline", default="on", choices=["on", "off"])
     ap.add_argument("--cpu-roots", type=int, default=1)
-    ap.add_argument("--no-extras", action="store_true", help="skip plain/e2e/roofline passes")
+    ap.add_argument("--no-extras", action="store_true", help="skip plain/e2e/roofline/batch/serve passes")
+    ap.add_argument("--no-batch-serve", action="store_true", help="skip the short batch and serve passes")
     ap.add_argument("--trace-out", default="")
     ap.add_argument("--bu-hub-first", action="store_true",
                     help="degree-aware bottom-up (Alg. 3 probe order, min-id parents restored after the loop)")
@@ -97,11 +98,15 @@ def hmean(x):
 
 # ---- CPU oracle leg (spawned process; never touches the GPU) -----------------------------
 
-def oracle_job(scale, edgefactor, seed, root_seed, nroots, warm, q, go):
+def oracle_job(scale, edgefactor, seed, root_seed, nroots, warm, q, go, save_dir=None):
     """Builds the oracle graph (untimed), then times serial oracle BFS from nroots roots.
-    Waits for `go`, so its host memory traffic never overlaps the GPU's timed passes."""
+    Waits for `go`, so its host memory traffic never overlaps the GPU's timed passes. With
+    save_dir, the first root's levels and parents are saved there (level.npy, parent.npy)
+    for an element-by-element comparison with the GPU's answer."""
     go.wait()
     try:
+        import numpy as np
+
         import graphgen
         from oracle import OracleGraph, traversed_tuples
         n = 1 << scale
@@ -113,24 +118,43 @@ def oracle_job(scale, edgefactor, seed, root_seed, nroots, warm, q, go):
         res = []
         for i in range(warm):
             og.bfs(int(roots[i % len(roots)]))
-        for r in roots[:nroots].tolist():
+        for i, r in enumerate(roots[:nroots].tolist()):
             t = time.perf_counter()
-            lv, _ = og.bfs(int(r))
+            lv, pa = og.bfs(int(r))
             dt = time.perf_counter() - t
             res.append((int(r), dt, traversed_tuples(e, lv)))
+            if i == 0 and save_dir:
+                np.save(os.path.join(save_dir, "level.npy"), lv)
+                np.save(os.path.join(save_dir, "parent.npy"), pa)
         q.put({"ok": True, "setup_s": setup, "runs": res})
     except Exception as ex:  # reported in the JSON line, never fatal
         q.put({"ok": False, "error": repr(ex)})
 
 
-def start_oracle(a, nroots, warm):
+def start_oracle(a, nroots, warm, save_dir=None):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     go = ctx.Event()
-    p = ctx.Process(target=oracle_job, args=(a.scale, a.edgefactor, a.seed, a.root_seed, nroots, warm, q, go),
-                    daemon=True)
+    p = ctx.Process(target=oracle_job,
+                    args=(a.scale, a.edgefactor, a.seed, a.root_seed, nroots, warm, q, go, save_dir), daemon=True)
     p.start()
     return p, q, go
+
+
+def parity_obj(cfg_name, root, got_level, got_parent, save_dir) -> dict:
+    """Element-by-element comparison of the GPU's answer for `root` with the oracle's."""
+    import numpy as np
+    try:
+        wl = np.load(os.path.join(save_dir, "level.npy"))
+        wp = np.load(os.path.join(save_dir, "parent.npy"))
+    except Exception as ex:
+        return {"config": cfg_name, "roots": 0, "equal": None, "error": repr(ex)}
+    ml = int((wl != got_level).sum())
+    mp_ = int((wp != got_parent).sum())
+    return {"config": cfg_name, "roots": 1, "root": int(root), "vertices": int(wl.size), "equal": ml == 0 and mp_ == 0,
+            "level_mismatches": ml, "parent_mismatches": mp_,
+            "how": "levels and min-id parents of gt_bfs (device, edge-tree BFS) against the CPU oracle (serial BFS "
+                   "on the unpeeled graph) from the same root, every vertex compared"}
 
 
 def oracle_result(p, q, go, timeout):
@@ -300,8 +324,10 @@ def main():
 
     # the oracle leg is spawned before the first GPU call
     oracle = None
+    oracle_dir = None
     if a.cpu_baseline == "on" and rank == 0 and world == 1:
-        oracle = start_oracle(a, a.cpu_roots, 0)
+        oracle_dir = tempfile.mkdtemp(prefix="gt_oracle_")
+        oracle = start_oracle(a, a.cpu_roots, 0, oracle_dir)
 
     import numpy as np
     import torch
@@ -428,6 +454,19 @@ def main():
             t = time.perf_counter()
             g.bfs(r, hp, hl, stream=stream)  # returns once the results are in host memory
             eg.append(tuples[i] / (time.perf_counter() - t) / 1e9)
+        # the host link itself: copy-engine device -> host rate into one pinned pair
+        db = torch.empty(2 * n, dtype=torch.int32, device=dev)
+        hb2 = torch.empty(2 * n, dtype=torch.int32).pin_memory()
+        hb2.copy_(db, non_blocking=True)
+        torch.cuda.synchronize()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record()
+        for _ in range(3):
+            hb2.copy_(db, non_blocking=True)
+        c1.record()
+        torch.cuda.synchronize()
+        link_gbs = 3 * 8 * n / (c0.elapsed_time(c1) * 1e-3) / 1e9
+        del db, hb2
         out["e2e"] = {"value": round(e_tup / e_time / 1e9, 3), "unit": UNIT, "h2d_bytes_per_step": 8 * len(roots),
                       "d2h_bytes_per_step": 8 * n * len(roots),
                       "how": f"gt_bfs_roots, {E2E_CHUNK} roots per call into pinned host parent/level buffers (one "
@@ -435,10 +474,10 @@ def main():
                              "host memory; traversed tuples / summed call time",
                       "single_call": {"value": round(hmean(eg), 3),
                                       "how": "gt_bfs per root into one pinned pair (returns after its copy); "
-                                             "harmonic mean"}}
+                                             "harmonic mean"},
+                      "link_d2h_gbs_copy_engine": round(link_gbs, 1),
+                      "link_bound_gteps": round(sum(tuples) / len(tuples) / (8 * n / (link_gbs * 1e9)) / 1e9, 1)}
 
-        if oracle is not None:
-            oracle[2].set()  # the timed and e2e passes are done: the CPU leg may start
         # roofline of the bottom-up kernel: work counts, then CUDA-event durations per launch
         g.set_tuning(count_work=1, launch_mode=1)
         counted = []
@@ -501,10 +540,32 @@ def main():
             json.dump({"roots": roots, "counted": counted, "timed": timed, "tuples": tuples,
                        "run_ms": run_ms, "phases": phases}, open(a.trace_out, "w"))
 
+        # the other half of the metric: batched and served queries/s (short passes)
+        if not a.no_batch_serve and rank == 0:
+            out["batch"] = batch_summary(batch_measure(a, gt, graphgen, torch, dev, ["single", "mixed"], True))
+            out["serve"] = serve_summary(a, serve_measure(gt, graphgen, torch, dev, [1000.0, 4000.0, 16000.0], 1.5,
+                                                          ["adaptive"], -1, a.serve_streams))
+            torch.cuda.empty_cache()
+
     if oracle is not None:
+        # every GPU pass is done: the CPU leg starts now (its graph build takes all host
+        # threads, which would disturb the host side of the passes above)
         out["cpu_baseline"] = cpu_baseline_obj(oracle_result(*oracle, timeout=1800), a.cpu_roots)
         if out["cpu_baseline"]["value"]:
             out["cpu_baseline"]["cores"] = 1
+            # the same root through gt_bfs, compared with the oracle's answer element by element
+            g.bfs(roots[0], parent, level, stream=stream)
+            torch.cuda.synchronize()
+            out["parity"] = parity_obj(cfg["workload"], roots[0], level.cpu().numpy(), parent.cpu().numpy(), oracle_dir)
+        for f in ("level.npy", "parent.npy"):
+            try:
+                os.unlink(os.path.join(oracle_dir, f))
+            except OSError:
+                pass
+        try:
+            os.rmdir(oracle_dir)
+        except OSError:
+            pass
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:
@@ -512,9 +573,14 @@ def main():
 
 
 def run_reference(a, world, rank):
-    """The CPU oracle timed as the reference arm: W + K steps, one seeded root per step."""
+    """The CPU oracle timed as the reference arm, one seeded root per step on the same graph
+    (built untimed). The W + K roots run concurrently on the host cores, one serial oracle
+    BFS per thread (the C oracle releases the GIL), so the whole run takes about two root
+    times instead of W + K; each step's GTEPS comes from its own root's time."""
     if rank != 0:
         return
+    from concurrent.futures import ThreadPoolExecutor
+
     import graphgen
     from oracle import OracleGraph, traversed_tuples
     n = 1 << a.scale
@@ -523,25 +589,34 @@ def run_reference(a, world, rank):
     og = OracleGraph(e, n)
     setup = time.time() - t0
     roots = graphgen.pick_roots(a.root_seed, n, a.roots, og.degree()).tolist()
-    for i in range(a.warmup):
-        og.bfs(roots[i % len(roots)])
-    runs = []
-    tt = time.perf_counter()
-    for i in range(a.steps):
+    cores = max(1, min(len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1),
+                       a.warmup + a.steps))
+
+    def one(i):
         r = roots[i % len(roots)]
         t = time.perf_counter()
         lv, _ = og.bfs(r)
         dt = time.perf_counter() - t
-        runs.append(traversed_tuples(e, lv) / dt / 1e9)
-    total = time.perf_counter() - tt
+        return i, dt, traversed_tuples(e, lv) if i >= a.warmup else 0
+
+    tt = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        done = list(ex.map(one, range(a.warmup + a.steps)))
+    wall = time.perf_counter() - tt
+    runs = [m / dt / 1e9 for (i, dt, m) in done if i >= a.warmup]
+    secs = [dt for (i, dt, m) in done if i >= a.warmup]
     v = hmean(runs)
     out = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": UNIT, "n_gpus": world,
-           "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(1e3 * total / a.steps, 1),
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(1e3 * sum(secs) / len(secs), 1),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
            "data": "synthetic", "config": workload(a),
-           "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": f"one seeded root per step on the same scale-{a.scale} graph; serial oracle "
-                                      f"BFS; oracle graph built untimed in {setup:.0f} s"},
+           "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"one seeded root per step on the same scale-{a.scale} graph (warm-up and "
+                                      f"timed roots together, {cores} at a time, one serial oracle BFS per host "
+                                      f"thread; each step timed on its own thread); oracle graph built untimed "
+                                      f"in {setup:.0f} s",
+                            "wall_s": round(wall, 1),
+                            "aggregate_gteps": round(sum(m for (i, _, m) in done if i >= a.warmup) / 1e9 / wall, 4)},
            "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -564,19 +639,10 @@ def _make_graph(gt, graphgen, torch, kind, a_, seed, dev):
     return g, e
 
 
-def run_batch_workload(a, rank, local):
-    """Batch workload: 64 roots in one lane word on R-MAT scale 24 (--batch-scale), and a mixed batch of 32 graphs
-    (R-MAT scales 14-22, uniform graphs of average degree 16), 64 roots each, every batch in
-    one persistent launch with autotuned parameters; against the same roots run one at a
-    time with gt_bfs. Queries/s and GTEPS-equivalent (traversed tuples / time)."""
-    import torch
-
-    import graphgen
-    import paper_2009_07463_gb300 as gt
-    if rank != 0:
-        return
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
+def batch_measure(a, gt, graphgen, torch, dev, parts, autotune) -> dict:
+    """Batched launches against the same roots one at a time (gt_bfs): R-MAT scale
+    a.batch_scale with 64 roots in one lane word ("single"), and 32 mixed graphs (R-MAT
+    scales 14-22, uniform graphs of average degree 16) with 64 roots each ("mixed")."""
     res = {}
 
     def timed(fn, reps):
@@ -594,7 +660,7 @@ def run_batch_workload(a, rank, local):
         graphs, roots, tuples = [], [], []
         for i, (kind, arg) in enumerate(specs):
             g, e = _make_graph(gt, graphgen, torch, kind, arg, 100 + i, dev)
-            if not a.no_batch_autotune:
+            if autotune:
                 g.autotune(nsample=4, seed=7)
             r = graphgen.pick_roots(3 + i, g.n, 64, g.degree()).tolist()
             lv = torch.empty(g.n, dtype=torch.int32, device=dev)
@@ -630,12 +696,37 @@ def run_batch_workload(a, rank, local):
             g.free()
         torch.cuda.empty_cache()
 
-    parts = [x for x in a.batch_parts.split(",") if x]
     if "single" in parts:
         measure([("rmat", a.batch_scale)], f"rmat_s{a.batch_scale}_64_roots")
     if "mixed" in parts:
         mixed = [("rmat", 14 + (i % 9)) for i in range(24)] + [("uniform", (1 << (15 + (i % 6)), 16)) for i in range(8)]
         measure(mixed, "mixed_32_graphs_64_roots_each")
+    return res
+
+
+def batch_summary(res: dict) -> dict:
+    return {"unit": "queries/s", "autotuned": True,
+            "parts": {k: {x: v[x] for x in ("queries", "batch_qps", "sequential_qps", "batch_ms", "sequential_ms",
+                                            "speedup")} for k, v in res.items()},
+            "how": "gt_bfs_batch (64-root lane words, one persistent launch, captured CUDA graph, autotuned) "
+                   "against the same roots one gt_bfs call at a time; CUDA events, mean of 3 launches"}
+
+
+def run_batch_workload(a, rank, local):
+    """Batch workload: 64 roots in one lane word on R-MAT scale 24 (--batch-scale), and a mixed batch of 32 graphs
+    (R-MAT scales 14-22, uniform graphs of average degree 16), 64 roots each, every batch in
+    one persistent launch with autotuned parameters; against the same roots run one at a
+    time with gt_bfs. Queries/s and GTEPS-equivalent (traversed tuples / time)."""
+    import torch
+
+    import graphgen
+    import paper_2009_07463_gb300 as gt
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    parts = [x for x in a.batch_parts.split(",") if x]
+    res = batch_measure(a, gt, graphgen, torch, dev, parts, not a.no_batch_autotune)
     head = res.get("mixed_32_graphs_64_roots_each") or next(iter(res.values()))
     out = {"metric": "batched BFS queries/s (64-root lane words, one persistent launch)",
            "value": head["batch_qps"], "unit": "queries/s", "n_gpus": 1,
@@ -693,22 +784,13 @@ def _serve_once(gt, graphs, bufs, RING, nq, gaps, gsel, roots, policy, join_leve
             "batched_launches": st["batches"], "joined": st["joined"], "early": st["early"]}
 
 
-def run_serve_workload(a, rank, local):
-    """Serving workload: 12 resident graphs (R-MAT scales 18-25 at edge factor 16; uniform
-    graphs of 2^20 vertices and average degree 8-32), a 48 GiB HBM budget, Poisson arrivals
-    of single-root queries at each stated rate (roots uniform over vertices of degree >= 1
-    of a uniformly chosen graph). Served under each dispatch policy vs the same arrival
-    schedule run by one worker with sequential gt_bfs calls. Queries/s and p50/p99 latency
-    (arrival -> results ready)."""
+def serve_measure(gt, graphgen, torch, dev, rates, seconds, policies, join_levels, streams) -> list:
+    """12 resident graphs (R-MAT scales 18-25 at edge factor 16; uniform graphs of 2^20
+    vertices and average degree 8-32), a 48 GiB HBM budget, Poisson arrivals of single-root
+    queries at each rate (roots uniform over vertices of degree >= 1 of a uniformly chosen
+    graph), served under each dispatch policy and run by one worker with sequential gt_bfs
+    calls on the same schedule."""
     import numpy as np
-    import torch
-
-    import graphgen
-    import paper_2009_07463_gb300 as gt
-    if rank != 0:
-        return
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
     specs = [("rmat", s) for s in range(18, 26)] + [("uniform", (1 << 20, d)) for d in (8, 16, 24, 32)]
     graphs, cand = [], []
     for i, (kind, arg) in enumerate(specs):
@@ -721,19 +803,17 @@ def run_serve_workload(a, rank, local):
     bufs = [[(torch.empty(g.n, dtype=torch.int32, device=dev), torch.empty(g.n, dtype=torch.int32, device=dev))
              for _ in range(RING)] for g in graphs]
     rng = np.random.default_rng(11)
-    rates = [float(x) for x in a.serve_rates.split(",") if x]
     results = []
     for rate in rates:
-        nq = int(rate * a.serve_seconds)
+        nq = int(rate * seconds)
         gaps = rng.exponential(1.0 / rate, size=nq)
         gsel = rng.integers(0, len(graphs), size=nq)
         roots = [int(cand[gi][rng.integers(0, cand[gi].size)]) for gi in gsel]
         served = {}
-        for pol in [x for x in a.serve_policies.split(",") if x]:
+        for pol in policies:
             served[pol] = _serve_once(gt, graphs, bufs, RING, nq, gaps, gsel, roots,
                                       {"adaptive": gt.GT_SERVE_ADAPTIVE, "batched": gt.GT_SERVE_BATCHED,
-                                       "single": gt.GT_SERVE_SINGLE}[pol], a.serve_join_levels,
-                                      a.serve_streams)
+                                       "single": gt.GT_SERVE_SINGLE}[pol], join_levels, streams)
         # sequential single-root calls on the same schedule (one worker, FIFO)
         lat2 = []
         stream = torch.cuda.current_stream()
@@ -755,7 +835,40 @@ def run_serve_workload(a, rank, local):
         seq = {"qps": round(nq / (t_end2 - t0), 1), "p50_us": round(1e6 * lat2s[nq // 2], 1),
                "p99_us": round(1e6 * lat2s[min(nq - 1, int(0.99 * nq))], 1)}
         results.append({"rate_qps": rate, "queries": nq, "served": served, "sequential": seq})
-    head = [x for x in a.serve_policies.split(",") if x][0]
+    del bufs
+    for g in graphs:
+        g.free()
+    torch.cuda.empty_cache()
+    return results
+
+
+def serve_summary(a, results) -> dict:
+    pol = next(iter(results[0]["served"]))
+    return {"unit": "queries/s", "policy": pol, "streams": a.serve_streams, "hbm_budget_gib": 48,
+            "graphs": "12 resident: rmat s18-25 ef16, uniform 2^20 deg 8/16/24/32",
+            "rates": [{"offered_qps": r["rate_qps"], "queries": r["queries"], "served_qps": r["served"][pol]["qps"],
+                       "p50_us": r["served"][pol]["p50_us"], "p99_us": r["served"][pol]["p99_us"],
+                       "sequential": r["sequential"]} for r in results],
+            "how": "Poisson arrivals of single-root queries; latency = arrival -> results in the caller's device "
+                   "buffers; sequential = one worker calling gt_bfs per query on the same schedule"}
+
+
+def run_serve_workload(a, rank, local):
+    """Serving workload (see serve_measure) at each --serve-rates rate under each
+    --serve-policies policy, against sequential gt_bfs calls on the same schedule."""
+    import torch
+
+    import graphgen
+    import paper_2009_07463_gb300 as gt
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rates = [float(x) for x in a.serve_rates.split(",") if x]
+    policies = [x for x in a.serve_policies.split(",") if x]
+    results = serve_measure(gt, graphgen, torch, dev, rates, a.serve_seconds, policies, a.serve_join_levels,
+                            a.serve_streams)
+    head = policies[0]
     best = max(results, key=lambda r: r["served"][head]["qps"])
     out = {"metric": "served BFS queries/s and p99 latency (continuous batching)", "value": best["served"][head]["qps"],
            "unit": "queries/s", "p99_us": best["served"][head]["p99_us"], "policy": head, "n_gpus": 1, "higher_is_better": True,

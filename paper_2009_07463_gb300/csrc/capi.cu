@@ -128,11 +128,41 @@ int bfs_common(gt_graph_t g, bool et, int64_t root, int32_t* parent, int32_t* le
   return rc;
 }
 
+// Copies one staged result (parent, level: n entries each) into page-locked host memory
+// from the SMs. A few CTAs writing over the host link reach its full rate (16 CTAs: 193
+// GB/s device to host on a GB300, the copy engine's rate there), and the copy then takes
+// the same path as the output pass's direct writes into host memory.
+__global__ void stage_to_host(const int32_t* __restrict__ sp, const int32_t* __restrict__ sl, int32_t* hp,
+                              int32_t* hl, int64_t n, int vec) {
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, T = (int64_t)gridDim.x * blockDim.x;
+  const int64_t n4 = vec ? n / 4 : 0;
+  for (int64_t i = t0; i < n4; i += T) {
+    reinterpret_cast<int4*>(hp)[i] = __ldcs(reinterpret_cast<const int4*>(sp) + i);
+    reinterpret_cast<int4*>(hl)[i] = __ldcs(reinterpret_cast<const int4*>(sl) + i);
+  }
+  for (int64_t i = 4 * n4 + t0; i < n; i += T) {
+    hp[i] = sp[i];
+    hl[i] = sl[i];
+  }
+}
+constexpr int STAGE_COPY_CTAS = 32;
+
+// Device-accessible address of page-locked host memory, or null for pageable memory.
+void* pinned_device_ptr(void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 // k edge-tree traversals in order on `s`. Roots with device outputs write them directly.
-// Roots with host outputs write a device staging pair (two pairs, alternating), and the
-// copy engine moves it to the host on the graph's copy stream while the traversal of the
-// next root already runs; the next root is always enqueued before the copy of the previous
-// one, so pageable copies (which block the calling thread) overlap it too.
+// Roots with host outputs write a device staging pair (two pairs, alternating), which is
+// moved to the host on the graph's copy stream while the traversal of the next root
+// already runs: by a small copy kernel into page-locked memory, by the copy engine into
+// pageable memory. The next root is always enqueued before the copy of the previous one,
+// so pageable copies (which block the calling thread) overlap it too.
 int bfs_roots(gt_graph_t g, const int64_t* roots, int32_t k, int32_t* const* parent, int32_t* const* level,
               cudaStream_t s) {
   std::vector<char> host(k);
@@ -181,8 +211,16 @@ int bfs_roots(gt_graph_t g, const int64_t* roots, int32_t k, int32_t* const* par
     const int32_t* dp = g->pipe_out + (int64_t)(2 * b) * g->n;
     const size_t bytes = sizeof(int32_t) * (size_t)g->n;
     int r = cuda_fail(cudaStreamWaitEvent(cs, ev_out[b], 0), "wait output");
-    if (!r) r = cuda_fail(cudaMemcpyAsync(parent[i], dp, bytes, cudaMemcpyDeviceToHost, cs), "copy parent");
-    if (!r) r = cuda_fail(cudaMemcpyAsync(level[i], dp + g->n, bytes, cudaMemcpyDeviceToHost, cs), "copy level");
+    int32_t* hp = (int32_t*)pinned_device_ptr(parent[i]);
+    int32_t* hl = (int32_t*)pinned_device_ptr(level[i]);
+    if (!r && hp && hl) {
+      const int vec = ((uintptr_t)hp % 16 == 0) && ((uintptr_t)hl % 16 == 0);
+      stage_to_host<<<STAGE_COPY_CTAS, 256, 0, cs>>>(dp, dp + g->n, hp, hl, g->n, vec);
+      r = cuda_fail(cudaGetLastError(), "copy kernel");
+    } else {
+      if (!r) r = cuda_fail(cudaMemcpyAsync(parent[i], dp, bytes, cudaMemcpyDeviceToHost, cs), "copy parent");
+      if (!r) r = cuda_fail(cudaMemcpyAsync(level[i], dp + g->n, bytes, cudaMemcpyDeviceToHost, cs), "copy level");
+    }
     if (!r) r = cuda_fail(cudaEventRecord(ev_copied[b], cs), "record copy");
     return r;
   };
