@@ -173,6 +173,15 @@ GT_API int gt_bfs_plain(gt_graph_t g, int64_t root, int32_t* parent, int32_t* le
 GT_API int gt_bfs_batch(const gt_graph_t* graphs, int32_t ngraphs, const int64_t* roots,
                         const int32_t* roots_per_graph, int32_t* const* parent, int32_t* const* level,
                         void* stream);
+/* Failure detection of the batched launches (no counterpart in the paper). Every wait of
+ * the persistent kernel at a grid barrier is bounded: after `polls` polls (default 2^26,
+ * seconds) the waiting CTA raises an error flag, every CTA leaves the kernel, and the call
+ * returns GT_ETIMEOUT with the device still usable. For tests of that path, this call sets
+ * the bound of later batched launches (gt_bfs_batch and the server's) and makes each
+ * barrier also wait for `extra` arrivals that never come, so that with extra > 0 every
+ * launch gives up at its first barrier after `polls` polls. polls = 0, extra = 0 restores
+ * the default. Process-wide; not for use while other threads launch batches. */
+GT_API void gt_test_batch_barrier(uint32_t polls, uint32_t extra);
 /* Autotuner: times edge-tree BFS from nsample seeded roots of degree >= 1 (and one batch
  * of up to 64 of them) under settings of gt_tuning, walking one parameter at a time, and
  * keeps the fastest in the handle (also copied to *best if non-null). Results do not

@@ -98,6 +98,7 @@ def lib():
                 "gt_serve_reset_stats": (ctypes.c_int, [p]),
                 "gt_serve_destroy": (ctypes.c_int, [p]),
                 "gt_count_traversed": (ctypes.c_int, [p, i64, p, i64, p, p]),
+                "gt_test_batch_barrier": (None, [ctypes.c_uint32, ctypes.c_uint32]),
                 "gt_strerror": (ctypes.c_char_p, [ctypes.c_int]),
                 "gt_last_error": (ctypes.c_char_p, []),
             }
@@ -403,6 +404,13 @@ class Server:
             self.destroy()
         except Exception:
             pass
+
+
+def gt_test_batch_barrier(polls: int = 0, extra: int = 0) -> None:
+    """Bounds of the grid-barrier waits of later batched launches (failure tests): with
+    extra > 0 every barrier waits for arrivals that never come and gives up after `polls`
+    polls, so the launch returns GT_ETIMEOUT. (0, 0) restores the default."""
+    lib().gt_test_batch_barrier(int(polls), int(extra))
 
 
 def gt_bfs_csr_noalloc(row, col, n: int, root: int, parent, level, stream=None) -> None:

@@ -28,6 +28,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "gt_device.cuh"
@@ -106,20 +107,31 @@ struct ResolveSeg {
 __device__ __forceinline__ uint64_t lanes_of(int nlanes) { return nlanes >= 64 ? ~0ull : (1ull << nlanes) - 1; }
 
 struct BatchCtl {
-  unsigned int bar;  // grid barrier arrivals
+  unsigned int bar;    // grid barrier arrivals
   int err;
-  int live;          // slots not done
-  int emit;          // slots with lanes to write at this level boundary
+  int live;            // slots not done
+  int emit;            // slots with lanes to write at this level boundary
+  unsigned int polls;  // a barrier wait gives up after this many polls
+  unsigned int extra;  // arrivals a barrier waits for beyond the grid's (0; failure tests only)
 };
 
+// Barrier wait bounds of the batched launches (see gt_test_batch_barrier): the default
+// gives up after 2^26 polls (seconds); a test can shorten it and add arrivals that never
+// come, so that the wait runs out.
+constexpr unsigned int BARRIER_POLLS = 1u << 26;
+std::atomic<unsigned int> g_barrier_polls{BARRIER_POLLS};
+std::atomic<unsigned int> g_barrier_extra{0};
+
 // Grid-wide barrier for a cooperative launch: arrivals counted on one word, each CTA
-// waits for its generation's total. Bounded: after ~2^26 polls (seconds) it raises err.
+// waits for its generation's total. Bounded: after bc->polls polls it raises err, and
+// every other waiting CTA sees err and leaves too.
 __device__ bool grid_barrier(BatchCtl* bc, unsigned int& gen) {
   __syncthreads();
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
     ++gen;
-    const unsigned int target = gen * gridDim.x;
+    const unsigned int target = gen * gridDim.x + bc->extra;
+    const unsigned int polls = bc->polls;
     __threadfence();
     atomicAdd(&bc->bar, 1u);
     int ok = 1;
@@ -129,7 +141,7 @@ __device__ bool grid_barrier(BatchCtl* bc, unsigned int& gen) {
         ok = 0;
         break;
       }
-      if (++spins > (1u << 26)) {
+      if (++spins > polls) {
         atomicExch(&bc->err, 1);
         ok = 0;
         break;
@@ -1006,7 +1018,7 @@ int batch_launch(BatchCtx* ctx, const SlotSpec* specs, int nspecs, int sm_share,
       hseg[(size_t)h * ns + i] = sg;
     }
   }
-  *hbc = BatchCtl{0u, 0, ns, 0};
+  *hbc = BatchCtl{0u, 0, ns, 0, g_barrier_polls.load(), g_barrier_extra.load()};
   char* base = (char*)ctx->dev;
   SlotDev* d_slots = (SlotDev*)base;
   SlotCtl* d_ctl = (SlotCtl*)(base + t_slots);
@@ -1042,6 +1054,11 @@ int batch_launch(BatchCtx* ctx, const SlotSpec* specs, int nspecs, int sm_share,
     ctx->key_bytes = bytes;
   }
   return cuda_fail(cudaGraphLaunch(ctx->exec, st), "batch graph launch");
+}
+
+void set_barrier_test(unsigned int polls, unsigned int extra) {
+  g_barrier_polls.store(polls ? polls : BARRIER_POLLS);
+  g_barrier_extra.store(extra);
 }
 
 int batch_status(const BatchCtx* ctx) {

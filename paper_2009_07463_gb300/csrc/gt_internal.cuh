@@ -235,6 +235,8 @@ size_t slot_bytes(const gt_graph* g);
 int batch_launch(BatchCtx* ctx, const SlotSpec* specs, int nspecs, int sm_share, cudaStream_t st,
                  BatchMailbox* mb = nullptr, int join_max = 0);
 int batch_status(const BatchCtx* ctx);
+// Barrier bounds of later batched launches (failure tests): polls = 0 restores the default.
+void set_barrier_test(unsigned int polls, unsigned int extra);
 void batch_ctx_free(BatchCtx* c);
 void free_batch_mem(gt_graph* g);
 
