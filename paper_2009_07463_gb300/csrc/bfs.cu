@@ -38,6 +38,7 @@ struct BfsArgs {
   int32_t* ulist;
   const int4* pre;         // adjacency prefix records (null: none)
   const int32_t* hub;      // highest-degree neighbours (degree-aware bottom-up; null: off)
+  int32_t sms;             // SMs of the device (grid of the one-CTA-per-SM kernels)
   BfsCtl* ctl;
   int32_t td_warp_min;
   int32_t td_cta_min;
@@ -46,8 +47,9 @@ struct BfsArgs {
   int32_t count_work;
 };
 
-BfsArgs make_args(const View& v, const gt_tuning& t) {
+BfsArgs make_args(const View& v, const gt_tuning& t, int sms) {
   BfsArgs a;
+  a.sms = std::max(1, sms);
   a.n = v.n;
   a.nnz = v.nnz;
   a.nwords = v.nwords;
@@ -611,6 +613,91 @@ __device__ __forceinline__ bool in_frontier(const uint32_t* __restrict__ vc, con
   return visited_bit(vc, u);
 }
 
+// Rows of the lanes in `lm` still open after the lane's own probes, scanned by the whole
+// warp: LS rows in flight at once (each a 32-entry window per step, so LS independent
+// load-and-probe chains per lane), a row that is settled (first visited neighbour in
+// position order, or its end) replaced at once by the next one of `lm`. The slot
+// variables are the same in every lane. A vertex found here gets its state and next-bitmap
+// bit from lane 0 (or, with OWN_BIT, sets `fj` in its own lane for the caller to write the
+// word); lane 0 counts the entries read.
+constexpr int LS = 2;
+
+// A Bloom filter of the current frontier in shared memory (2^19 bits, two hashes of the
+// vertex id): a vertex that fails it is certainly not in the frontier, so the bitmap probe
+// in L2 is only made for the few that pass.
+constexpr int BLOOM_LOG = 19;
+constexpr int BLOOM_WORDS = (1 << BLOOM_LOG) / 32;
+constexpr int64_t BLOOM_MAX_FRONTIER = 65536;  // frontiers up to this size get a filter
+
+__device__ __forceinline__ uint32_t bloom_h1(int32_t u) { return ((uint32_t)u * 0x9E3779B1u) >> (32 - BLOOM_LOG); }
+__device__ __forceinline__ uint32_t bloom_h2(int32_t u) { return ((uint32_t)u * 0x85EBCA77u) >> (32 - BLOOM_LOG); }
+__device__ __forceinline__ bool bloom_maybe(const uint32_t* bf, int32_t u) {
+  const uint32_t h1 = bloom_h1(u), h2 = bloom_h2(u);
+  return (bf[h1 >> 5] >> (h1 & 31)) & (bf[h2 >> 5] >> (h2 & 31)) & 1u;
+}
+
+template <bool HASH, bool OWN_BIT, bool BLOOM = false>
+__device__ __forceinline__ void bu_long_rows(const BfsArgs& a, const uint32_t* __restrict__ vc,
+                                             const int32_t* __restrict__ s_hash, uint32_t* vn, uint64_t hi,
+                                             unsigned lm, int32_t wj, int64_t limj, int64_t ej, int32_t dj, bool& fj,
+                                             int64_t& nf, int64_t& mf, int64_t& examined,
+                                             const uint32_t* bf = nullptr) {
+  const int lane = threadIdx.x & 31;
+  int32_t sw[LS], sr[LS], ss[LS];  // slot: vertex (-1 free), entries left, lane it came from
+  int64_t sp[LS];                  // slot: next entry
+#pragma unroll
+  for (int k = 0; k < LS; ++k) {
+    sw[k] = -1;
+    sr[k] = ss[k] = 0;
+    sp[k] = 0;
+  }
+  for (;;) {
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < LS; ++k) {
+      if (sw[k] < 0 && lm) {
+        const int src = __ffs(lm) - 1;
+        lm &= lm - 1;
+        sw[k] = __shfl_sync(FULL, wj, src);
+        sp[k] = __shfl_sync(FULL, limj, src);
+        sr[k] = (int32_t)(__shfl_sync(FULL, ej, src) - sp[k]);
+        ss[k] = src;
+      }
+      any |= sw[k] >= 0;
+    }
+    if (!any) break;
+    int32_t uu[LS];
+    bool hh[LS];
+#pragma unroll
+    for (int k = 0; k < LS; ++k) uu[k] = (sw[k] >= 0 && lane < sr[k]) ? a.col[sp[k] + lane] : -1;
+#pragma unroll
+    for (int k = 0; k < LS; ++k)
+      hh[k] = uu[k] >= 0 && (!BLOOM || bloom_maybe(bf, uu[k])) && in_frontier<HASH>(vc, s_hash, uu[k]);
+#pragma unroll
+    for (int k = 0; k < LS; ++k) {
+      if (sw[k] < 0) continue;
+      const unsigned hm = __ballot_sync(FULL, hh[k]);
+      if (hm) {
+        const int32_t par = __shfl_sync(FULL, uu[k], __ffs(hm) - 1);
+        if (lane == 0) {
+          examined += __ffs(hm);
+          a.state[sw[k]] = hi | (uint32_t)par;
+          if (!OWN_BIT) atomicOr(&vn[sw[k] >> 5], 1u << (sw[k] & 31));
+          ++nf;
+          mf += a.row[sw[k] + 1] - a.row[sw[k]];
+        }
+        if (OWN_BIT && lane == ss[k]) fj = true;
+        sw[k] = -1;
+      } else {
+        if (lane == 0) examined += min(32, sr[k]);
+        sp[k] += 32;
+        sr[k] -= 32;
+        if (sr[k] <= 0) sw[k] = -1;
+      }
+    }
+  }
+}
+
 // Scan: a warp takes 32 x BU_V consecutive listed vertices. With prefix records (PRE),
 // each lane reads the records of its BU_V vertices (degree and first three neighbours,
 // 16 bytes each, in list order) and tests all listed neighbours at once; only a vertex
@@ -765,41 +852,8 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) bfs_bu_scan(BfsArgs a) {
       if (fnd && lane == __ffs(peers) - 1) atomicOr(&vn[w[j] >> 5], bits);
       const int64_t lim = min(e[j], s[j] + (int64_t)alone);  // where this lane's own probes stopped
       unsigned lm = __ballot_sync(FULL, w[j] >= 0 && !fnd && lim < e[j]);
-      while (lm) {
-        const int src = __ffs(lm) - 1;
-        lm &= lm - 1;
-        const int32_t w2 = __shfl_sync(FULL, w[j], src);
-        const int64_t s2 = __shfl_sync(FULL, lim, src), e2 = __shfl_sync(FULL, e[j], src);
-        const int32_t d2 = __shfl_sync(FULL, d[j], src);
-        int32_t par2 = -1;
-        for (int64_t b0 = s2; b0 < e2 && par2 < 0; b0 += 32 * CW) {
-          // CW windows of 32 neighbours in flight per lane, resolved in order
-          int32_t uu[CW];
-          bool hh[CW];
-#pragma unroll
-          for (int t = 0; t < CW; ++t) {
-            const int64_t k2 = b0 + 32 * t + lane;
-            uu[t] = k2 < e2 ? a.col[k2] : -1;
-          }
-#pragma unroll
-          for (int t = 0; t < CW; ++t) hh[t] = uu[t] >= 0 && in_frontier<HASH>(vc, s_hash, uu[t]);
-#pragma unroll
-          for (int t = 0; t < CW; ++t) {
-            const unsigned hm = __ballot_sync(FULL, hh[t]);
-            if (par2 < 0 && hm) {
-              par2 = __shfl_sync(FULL, uu[t], __ffs(hm) - 1);
-              if (lane == 0) examined += 32 * t + __ffs(hm);
-            }
-          }
-          if (par2 < 0 && lane == 0) examined += min((int64_t)(32 * CW), e2 - b0);
-        }
-        if (par2 >= 0 && lane == 0) {
-          a.state[w2] = hi | (uint32_t)par2;
-          atomicOr(&vn[w2 >> 5], 1u << (w2 & 31));
-          ++nf;
-          mf += d2;
-        }
-      }
+      bool unused = false;
+      bu_long_rows<HASH, false>(a, vc, s_hash, vn, hi, lm, w[j], lim, e[j], d[j], unused, nf, mf, examined);
     }
   }
   block_commit(a, nf, mf, examined);
@@ -814,10 +868,35 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) bfs_bu_scan(BfsArgs a) {
 // above (record probes, lane continuation, whole-warp continuation for long rows). The
 // warp owns its words of the next bitmap and writes each one whole (visited bits | bits
 // found), so neither the gather pass's copy nor per-word atomics are needed.
-__global__ void __launch_bounds__(BFS_THREADS, 4) bfs_bu_stream(BfsArgs a) {
+// COUNT: also count the adjacency entries read (the trace's `examined`; off in timed runs,
+// where the counting would only add instructions).
+// BLOOM: the step follows a top-down step with a frontier of at most BLOOM_MAX_FRONTIER
+// vertices (all in the queue); every CTA first builds the frontier's Bloom filter in shared
+// memory and probes the bitmap only for neighbours that pass it. For an unvisited vertex
+// both tests agree, since its visited neighbours are exactly its frontier ones. One
+// 1024-thread CTA per SM holds one copy of the filter, so L1 keeps most of its capacity.
+template <bool COUNT, bool BLOOM, int T, int MINB>
+__global__ void __launch_bounds__(T, MINB) bfs_bu_stream(BfsArgs a) {
+  extern __shared__ uint32_t s_bloom[];
   BfsCtl* ctl = a.ctl;
   const uint32_t* __restrict__ vc = ctl->vcur ? a.vis1 : a.vis0;
   uint32_t* vn = ctl->vcur ? a.vis0 : a.vis1;
+  if (BLOOM) {
+    for (int i = threadIdx.x; i < BLOOM_WORDS; i += T) s_bloom[i] = 0u;
+    __syncthreads();
+    for (int b = 0; b < NBINS; ++b) {
+      const int32_t* q = queue_of(a, ctl->cur, b);
+      const int64_t nb = ctl->bin_n[b];
+      for (int64_t i = threadIdx.x; i < nb; i += T) {
+        const int32_t u = q[i];
+        const uint32_t h1 = bloom_h1(u), h2 = bloom_h2(u);
+        atomicOr(&s_bloom[h1 >> 5], 1u << (h1 & 31));
+        atomicOr(&s_bloom[h2 >> 5], 1u << (h2 & 31));
+      }
+    }
+    __syncthreads();
+  }
+  const uint32_t* bf = s_bloom;
   const uint64_t hi = (uint64_t)(uint32_t)(ctl->level + 1) << 32;
   const int lane = threadIdx.x & 31;
   const int64_t gw = gtid() >> 5, nw = gthreads() >> 5;
@@ -825,122 +904,83 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) bfs_bu_stream(BfsArgs a) {
   int64_t nf = 0, mf = 0, examined = 0;
   for (int64_t w0 = gw * BU_V; w0 < a.nwords; w0 += nw * BU_V) {
     uint32_t vw[BU_V];
-    int32_t w[BU_V], par[BU_V], d[BU_V];
-    int64_t s[BU_V], e[BU_V];
-    int4 r[BU_V];
+    int4 r[BU_V];  // prefix record; degree 0 for a visited vertex or one past n
 #pragma unroll
     for (int j = 0; j < BU_V; ++j) {
       vw[j] = __ldg(&vc[w0 + j]);
       const int64_t v = (w0 + j) * 32 + lane;
-      r[j] = v < a.n ? __ldg(&a.pre[v]) : make_int4(0, -1, -1, -1);
+      r[j] = v < a.n ? __ldg(&a.pre[v]) : make_int4(0, 0, 0, 0);
     }
 #pragma unroll
-    for (int j = 0; j < BU_V; ++j) {
-      const int64_t v = (w0 + j) * 32 + lane;
-      w[j] = (v < a.n && !((vw[j] >> lane) & 1u)) ? (int32_t)v : -1;  // padding bits are set
-      if (w[j] < 0) r[j] = make_int4(0, -1, -1, -1);
-    }
+    for (int j = 0; j < BU_V; ++j)
+      if ((vw[j] >> lane) & 1u) r[j].x = 0;  // visited (padding bits past n are set)
     uint32_t b0[BU_V], b1[BU_V], b2[BU_V];
 #pragma unroll
     for (int j = 0; j < BU_V; ++j) {
-      b0[j] = r[j].y >= 0 ? __ldg(&vc[r[j].y >> 5]) : 0u;
-      b1[j] = r[j].z >= 0 ? __ldg(&vc[r[j].z >> 5]) : 0u;
-      b2[j] = r[j].w >= 0 ? __ldg(&vc[r[j].w >> 5]) : 0u;
+      b0[j] = (r[j].x > 0 && (!BLOOM || bloom_maybe(bf, r[j].y))) ? __ldg(&vc[r[j].y >> 5]) : 0u;
+      b1[j] = (r[j].x > 1 && (!BLOOM || bloom_maybe(bf, r[j].z))) ? __ldg(&vc[r[j].z >> 5]) : 0u;
+      b2[j] = (r[j].x > 2 && (!BLOOM || bloom_maybe(bf, r[j].w))) ? __ldg(&vc[r[j].w >> 5]) : 0u;
     }
+    int32_t par[BU_V], lr[BU_V];  // parent (-1: none yet); CSR entries left to the lane
+    const int32_t* cp[BU_V];       // the vertex's entries after its record
 #pragma unroll
     for (int j = 0; j < BU_V; ++j) {
-      const bool h0 = r[j].y >= 0 && ((b0[j] >> (r[j].y & 31)) & 1u);
-      const bool h1 = r[j].z >= 0 && ((b1[j] >> (r[j].z & 31)) & 1u);
-      const bool h2 = r[j].w >= 0 && ((b2[j] >> (r[j].w & 31)) & 1u);
+      const bool h0 = (b0[j] >> (r[j].y & 31)) & 1u;
+      const bool h1 = (b1[j] >> (r[j].z & 31)) & 1u;
+      const bool h2 = (b2[j] >> (r[j].w & 31)) & 1u;
       par[j] = h0 ? r[j].y : h1 ? r[j].z : h2 ? r[j].w : -1;
-      d[j] = r[j].x;
-      examined += h0 ? 1 : h1 ? 2 : h2 ? 3 : min(r[j].x, 3);
-      s[j] = 0;
-      e[j] = 0;
-      if (w[j] >= 0 && par[j] < 0 && d[j] > 3) {
-        s[j] = a.row[w[j]] + 3;
-        e[j] = s[j] - 3 + d[j];
-      }
+      if (COUNT) examined += h0 ? 1 : h1 ? 2 : h2 ? 3 : min(r[j].x, 3);
+      const bool open = par[j] < 0 && r[j].x > 3;
+      lr[j] = open ? min(r[j].x - 3, alone) : 0;
+      cp[j] = open ? a.col + a.row[(w0 + j) * 32 + lane] + 3 : a.col;
     }
-    int64_t nx[BU_V];
-#pragma unroll
-    for (int j = 0; j < BU_V; ++j) nx[j] = s[j];
-    for (int rd = 0; rd < alone; ++rd) {
-      int32_t u[BU_V];
+    // lane continuation, depth by depth: at every depth the open vertices of this lane
+    // issue their loads together, so BU_V dependent chains overlap
+    for (int t = 0; t < alone; ++t) {
       bool any = false;
+      int32_t u[BU_V];
 #pragma unroll
       for (int j = 0; j < BU_V; ++j) {
-        u[j] = -1;
-        if (par[j] < 0 && nx[j] < e[j] && nx[j] - s[j] < alone) {
-          u[j] = a.col[nx[j]];
-          any = true;
-        }
+        any |= t < lr[j];
+        u[j] = t < lr[j] ? cp[j][t] : 0;
       }
       if (!any) break;
       uint32_t pw[BU_V];
 #pragma unroll
-      for (int j = 0; j < BU_V; ++j) pw[j] = u[j] >= 0 ? __ldg(&vc[u[j] >> 5]) : 0u;
+      for (int j = 0; j < BU_V; ++j)
+        pw[j] = (t < lr[j] && (!BLOOM || bloom_maybe(bf, u[j]))) ? __ldg(&vc[u[j] >> 5]) : 0u;
 #pragma unroll
       for (int j = 0; j < BU_V; ++j) {
-        if (u[j] >= 0) {
-          ++nx[j];
-          if ((pw[j] >> (u[j] & 31)) & 1u) par[j] = u[j];
+        if (t < lr[j] && ((pw[j] >> (u[j] & 31)) & 1u)) {
+          par[j] = u[j];
+          if (COUNT) examined += t + 1;
+          lr[j] = 0;  // settled: no more probes
         }
       }
     }
 #pragma unroll
-    for (int j = 0; j < BU_V; ++j) examined += nx[j] - s[j];
-#pragma unroll
     for (int j = 0; j < BU_V; ++j) {
+      const int32_t v = (int32_t)((w0 + j) * 32 + lane);
+      const int32_t cnt = r[j].x - 3;  // entries after the record
+      if (COUNT && par[j] < 0 && cnt > 0) examined += min(cnt, alone);
       bool fj = par[j] >= 0;
       if (fj) {
-        a.state[w[j]] = hi | (uint32_t)par[j];
+        a.state[v] = hi | (uint32_t)par[j];
         ++nf;
-        mf += d[j];
+        mf += r[j].x;
       }
-      const int64_t lim = min(e[j], s[j] + (int64_t)alone);  // where this lane's own probes stopped
-      unsigned lm = __ballot_sync(FULL, w[j] >= 0 && !fj && lim < e[j]);
-      while (lm) {
-        const int src = __ffs(lm) - 1;
-        lm &= lm - 1;
-        const int32_t w2 = __shfl_sync(FULL, w[j], src);
-        const int64_t s2 = __shfl_sync(FULL, lim, src), e2 = __shfl_sync(FULL, e[j], src);
-        const int32_t d2 = __shfl_sync(FULL, d[j], src);
-        int32_t par2 = -1;
-        for (int64_t c0 = s2; c0 < e2 && par2 < 0; c0 += 32 * CW) {
-          int32_t uu[CW];
-          bool hh[CW];
-#pragma unroll
-          for (int t = 0; t < CW; ++t) {
-            const int64_t k2 = c0 + 32 * t + lane;
-            uu[t] = k2 < e2 ? a.col[k2] : -1;
-          }
-#pragma unroll
-          for (int t = 0; t < CW; ++t) hh[t] = uu[t] >= 0 && visited_bit(vc, uu[t]);
-#pragma unroll
-          for (int t = 0; t < CW; ++t) {
-            const unsigned hm = __ballot_sync(FULL, hh[t]);
-            if (par2 < 0 && hm) {
-              par2 = __shfl_sync(FULL, uu[t], __ffs(hm) - 1);
-              if (lane == 0) examined += 32 * t + __ffs(hm);
-            }
-          }
-          if (par2 < 0 && lane == 0) examined += min((int64_t)(32 * CW), e2 - c0);
-        }
-        if (par2 >= 0) {
-          if (lane == 0) {
-            a.state[w2] = hi | (uint32_t)par2;
-            ++nf;
-            mf += d2;
-          }
-          if (lane == src) fj = true;
-        }
+      const bool lng = !fj && cnt > alone;
+      const unsigned lm = __ballot_sync(FULL, lng);
+      if (lm) {
+        const int64_t s0 = lng ? (int64_t)(cp[j] - a.col) : 0;
+        bu_long_rows<false, true, BLOOM>(a, vc, nullptr, vn, hi, lm, v, s0 + alone, s0 + cnt, r[j].x, fj, nf,
+                                         mf, examined, bf);
       }
       const unsigned fb = __ballot_sync(FULL, fj);
       if (lane == j) vn[w0 + j] = vw[j] | fb;
     }
   }
-  block_commit(a, nf, mf, examined);
+  block_commit<T / 32>(a, nf, mf, examined);
 }
 
 // ---- level control -----------------------------------------------------------------
@@ -999,9 +1039,12 @@ __global__ void bfs_decide(BfsArgs a, cudaGraphConditionalHandle h_loop, cudaGra
     c->need_queue = (dir == DIR_BU && nd == DIR_TD);
     c->bu_hash = c->need_mark && nn <= HASH_CAP;
     c->n_visited += nn;
-    // stream when more than half of the vertices are unvisited and records exist (the
+    // stream while more than a sixth of the vertices are unvisited (measured at scale 26:
+    // 1/2, 1/3, 1/4, 1/6, 1/10, always; 1/6 to 1/10 best) and records exist (the
     // degree-aware option works on the gathered list)
-    c->bu_stream = a.pre && !a.hub && (a.n - c->n_visited) * 2 > a.n;
+    c->bu_stream = a.pre && !a.hub && (a.n - c->n_visited) * 6 > a.n;
+    // a small frontier right after a top-down step (it is all in the queue): filter it
+    c->bu_bloom = c->bu_stream && c->need_mark && nn <= BLOOM_MAX_FRONTIER;
     c->dir = nd;
   }
   if (use_handles) {
@@ -1012,10 +1055,11 @@ __global__ void bfs_decide(BfsArgs a, cudaGraphConditionalHandle h_loop, cudaGra
 
 // Which step kernels run next: 0 top-down, 1 bottom-up, 2 mark + bottom-up,
 // 3 queue rebuild + top-down, 4 mark + bottom-up probing a shared-memory frontier set,
-// 5 streaming bottom-up, 6 mark + streaming bottom-up.
+// 5 streaming bottom-up, 6 mark + streaming bottom-up, 7 mark + streaming bottom-up with a
+// Bloom filter of the frontier in shared memory.
 __device__ __forceinline__ unsigned step_kind(const BfsCtl* c) {
   if (c->dir == DIR_TD) return c->need_queue ? 3u : 0u;
-  if (c->need_mark) return c->bu_hash ? 4u : (c->bu_stream ? 6u : 2u);
+  if (c->need_mark) return c->bu_bloom ? 7u : c->bu_hash ? 4u : (c->bu_stream ? 6u : 2u);
   return c->bu_stream ? 5u : 1u;
 }
 
@@ -1055,6 +1099,7 @@ __device__ void ctl_begin(const BfsArgs& a, int32_t start, int32_t start_level, 
   c->need_queue = 0;
   c->bu_hash = 0;
   c->bu_stream = 0;
+  c->bu_bloom = 0;
   c->alpha = alpha;
   c->beta = beta;
   c->force = force;
@@ -1237,8 +1282,9 @@ int grid_stream(const gt_graph* g, int64_t work) {
   return (int)std::max<int64_t>(1, std::min(want, cap));
 }
 
-constexpr int NKINDS = 7;
+constexpr int NKINDS = 8;
 constexpr size_t HASH_SMEM = sizeof(int32_t) * HASH_SLOTS;
+constexpr size_t BLOOM_SMEM = sizeof(uint32_t) * BLOOM_WORDS;
 
 // Lets the shared-memory-set variant of the scan take its 64 KB of dynamic shared memory.
 int prepare_kernels() {
@@ -1249,21 +1295,40 @@ int prepare_kernels() {
     rc = cuda_fail(cudaFuncSetAttribute(bfs_bu_scan<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)HASH_SMEM),
                    "scan shared memory");
+  if (rc == GT_OK)
+    rc = cuda_fail(cudaFuncSetAttribute(bfs_bu_stream<false, true, 1024, 1>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BLOOM_SMEM),
+                   "stream shared memory");
+  if (rc == GT_OK)
+    rc = cuda_fail(cudaFuncSetAttribute(bfs_bu_stream<true, true, 1024, 1>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BLOOM_SMEM),
+                   "stream shared memory");
   return rc;
 }
 
 // The step kernels of one level: 0 top-down, 1 bottom-up (gather + scan), 2 mark +
 // bottom-up, 3 queue rebuild + top-down, 4 mark + bottom-up with the frontier set in
-// shared memory, 5 streaming bottom-up, 6 mark + streaming bottom-up.
+// shared memory, 5 streaming bottom-up, 6 mark + streaming bottom-up, 7 mark + streaming
+// bottom-up with a Bloom filter of the frontier.
 void launch_step(int kind, const BfsArgs& a, int grid, cudaStream_t s) {
   if (kind == 3) bfs_queue_from_bitmap<<<grid, BFS_THREADS, 0, s>>>(a);
   if (kind == 0 || kind == 3) {
     bfs_td<<<grid, BFS_THREADS, 0, s>>>(a);
     return;
   }
-  if (kind == 2 || kind == 4 || kind == 6) bfs_mark<<<grid, BFS_THREADS, 0, s>>>(a);
+  if (kind == 2 || kind == 4 || kind == 6 || kind == 7) bfs_mark<<<grid, BFS_THREADS, 0, s>>>(a);
   if (kind == 5 || kind == 6) {
-    bfs_bu_stream<<<grid, BFS_THREADS, 0, s>>>(a);
+    if (a.count_work)
+      bfs_bu_stream<true, false, BFS_THREADS, 4><<<grid, BFS_THREADS, 0, s>>>(a);
+    else
+      bfs_bu_stream<false, false, BFS_THREADS, 4><<<grid, BFS_THREADS, 0, s>>>(a);
+    return;
+  }
+  if (kind == 7) {
+    if (a.count_work)
+      bfs_bu_stream<true, true, 1024, 1><<<a.sms, 1024, BLOOM_SMEM, s>>>(a);
+    else
+      bfs_bu_stream<false, true, 1024, 1><<<a.sms, 1024, BLOOM_SMEM, s>>>(a);
     return;
   }
   bfs_bu_gather<<<grid, BFS_THREADS, 0, s>>>(a);
@@ -1281,9 +1346,9 @@ void launch_step(int kind, const BfsArgs& a, int grid, cudaStream_t s) {
   }
 }
 
-unsigned host_step_kind(int dir, int need_mark, int need_queue, int bu_hash, int bu_stream) {
+unsigned host_step_kind(int dir, int need_mark, int need_queue, int bu_hash, int bu_stream, int bu_bloom) {
   if (dir == DIR_TD) return need_queue ? 3u : 0u;
-  if (need_mark) return bu_hash ? 4u : (bu_stream ? 6u : 2u);
+  if (need_mark) return bu_bloom ? 7u : bu_hash ? 4u : (bu_stream ? 6u : 2u);
   return bu_stream ? 5u : 1u;
 }
 
@@ -1293,7 +1358,7 @@ unsigned host_step_kind(int dir, int need_mark, int need_queue, int bu_hash, int
 // Both handles are created on the top graph with a launch default (loop: 1; kind: the
 // first step of a fresh traversal); decide sets them for the next iteration.
 int build_loop_graph(gt_graph* g, const View& v, cudaGraphExec_t* out) {
-  const BfsArgs a = make_args(v, g->tuning);
+  const BfsArgs a = make_args(v, g->tuning, g->launch.sms);
   const int grid = g->launch.grid;
   cudaGraph_t graph = nullptr;
   cudaStream_t cs = nullptr;
@@ -1371,10 +1436,10 @@ int run_level_loop(gt_graph* g, View& v, int which, cudaStream_t s) {
     return cuda_fail(cudaGraphLaunch(g->loop_exec[which], s), "graph launch");
   }
   // host-driven: one small readback per level
-  const BfsArgs a = make_args(v, t);
+  const BfsArgs a = make_args(v, t, g->launch.sms);
   const int grid = g->launch.grid;
   struct Head {
-    int32_t level, dir, done, cur, vcur, need_mark, need_queue, bu_hash, bu_stream;
+    int32_t level, dir, done, cur, vcur, need_mark, need_queue, bu_hash, bu_stream, bu_bloom;
   } h{};
   const cudaGraphConditionalHandle none = 0;
   int timed_steps = 0;
@@ -1396,7 +1461,7 @@ int run_level_loop(gt_graph* g, View& v, int which, cudaStream_t s) {
       }
       cudaEventRecord(g->step_events[2 * guard], s);
     }
-    launch_step((int)host_step_kind(h.dir, h.need_mark, h.need_queue, h.bu_hash, h.bu_stream), a, grid, s);
+    launch_step((int)host_step_kind(h.dir, h.need_mark, h.need_queue, h.bu_hash, h.bu_stream, h.bu_bloom), a, grid, s);
     if (timed) {
       cudaEventRecord(g->step_events[2 * guard + 1], s);
       ++timed_steps;
@@ -1424,7 +1489,7 @@ int run_bfs(gt_graph* g, View& v, bool et, int64_t root, int32_t* parent, int32_
     const int rc0 = ensure_hub(g, v, s);
     if (rc0 != GT_OK) return rc0;
   }
-  const BfsArgs a = make_args(v, t);
+  const BfsArgs a = make_args(v, t, g->launch.sms);
   const bool timed = t.time_kernels;
   if (timed && !g->phase_events[0])
     for (int i = 0; i < 4; ++i) cudaEventCreate(&g->phase_events[i]);
@@ -1584,7 +1649,7 @@ extern "C" GT_API int gt_bfs_csr_noalloc(const int64_t* row, const int32_t* col,
   v.ulist = (int32_t*)p;
   gt_tuning t;
   gt_tuning_default(&t);
-  const BfsArgs a = make_args(v, t);
+  const BfsArgs a = make_args(v, t, sms);
   const int grid = sms * std::max(1, t.blocks_per_sm);
   // state and the first bitmap start cleared; the control block is rewritten by the start
   // kernel; queue and list entries are only read below the counts the kernels set

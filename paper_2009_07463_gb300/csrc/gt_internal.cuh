@@ -39,6 +39,7 @@ struct BfsCtl {
   int32_t need_queue; // 1: rebuild the current queue from the bitmaps before a top-down step
   int32_t bu_hash;    // 1: the bottom-up step may probe a shared-memory copy of the frontier
   int32_t bu_stream;  // 1: the bottom-up step streams all vertices (most are unvisited)
+  int32_t bu_bloom;   // 1: ... and probes a shared-memory filter of a small frontier first
   int32_t nlevels;    // steps taken
   int64_t n_visited;  // vertices visited so far
   int64_t n_f;        // current frontier vertices
