@@ -622,18 +622,19 @@ __device__ __forceinline__ bool in_frontier(const uint32_t* __restrict__ vc, con
 // word); lane 0 counts the entries read.
 constexpr int LS = 2;
 
-// A Bloom filter of the current frontier in shared memory (2^19 bits, two hashes of the
-// vertex id): a vertex that fails it is certainly not in the frontier, so the bitmap probe
-// in L2 is only made for the few that pass.
+// A filter of the current frontier in shared memory: 2^19 bits, one multiplicative hash of
+// the vertex id (a Bloom filter with one hash function). A vertex whose bit is clear is
+// certainly not in the frontier, so the bitmap probe in L2 is only made for the rest: the
+// frontier itself and about F / 2^19 of the others (a second hash function lowered that
+// share but cost more instructions than it saved: 852-855 against 863-866 GTEPS at scale 26).
 constexpr int BLOOM_LOG = 19;
 constexpr int BLOOM_WORDS = (1 << BLOOM_LOG) / 32;
 constexpr int64_t BLOOM_MAX_FRONTIER = 65536;  // frontiers up to this size get a filter
 
 __device__ __forceinline__ uint32_t bloom_h1(int32_t u) { return ((uint32_t)u * 0x9E3779B1u) >> (32 - BLOOM_LOG); }
-__device__ __forceinline__ uint32_t bloom_h2(int32_t u) { return ((uint32_t)u * 0x85EBCA77u) >> (32 - BLOOM_LOG); }
 __device__ __forceinline__ bool bloom_maybe(const uint32_t* bf, int32_t u) {
-  const uint32_t h1 = bloom_h1(u), h2 = bloom_h2(u);
-  return (bf[h1 >> 5] >> (h1 & 31)) & (bf[h2 >> 5] >> (h2 & 31)) & 1u;
+  const uint32_t h1 = bloom_h1(u);
+  return (bf[h1 >> 5] >> (h1 & 31)) & 1u;
 }
 
 template <bool HASH, bool OWN_BIT, bool BLOOM = false>
@@ -871,7 +872,7 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) bfs_bu_scan(BfsArgs a) {
 // COUNT: also count the adjacency entries read (the trace's `examined`; off in timed runs,
 // where the counting would only add instructions).
 // BLOOM: the step follows a top-down step with a frontier of at most BLOOM_MAX_FRONTIER
-// vertices (all in the queue); every CTA first builds the frontier's Bloom filter in shared
+// vertices (all in the queue); every CTA first builds the frontier's filter in shared
 // memory and probes the bitmap only for neighbours that pass it. For an unvisited vertex
 // both tests agree, since its visited neighbours are exactly its frontier ones. One
 // 1024-thread CTA per SM holds one copy of the filter, so L1 keeps most of its capacity.
@@ -889,9 +890,8 @@ __global__ void __launch_bounds__(T, MINB) bfs_bu_stream(BfsArgs a) {
       const int64_t nb = ctl->bin_n[b];
       for (int64_t i = threadIdx.x; i < nb; i += T) {
         const int32_t u = q[i];
-        const uint32_t h1 = bloom_h1(u), h2 = bloom_h2(u);
+        const uint32_t h1 = bloom_h1(u);
         atomicOr(&s_bloom[h1 >> 5], 1u << (h1 & 31));
-        atomicOr(&s_bloom[h2 >> 5], 1u << (h2 & 31));
       }
     }
     __syncthreads();
