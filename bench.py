@@ -676,6 +676,8 @@ def batch_measure(a, gt, graphgen, torch, dev, parts, autotune) -> dict:
         outs_p = [torch.empty((64, g.n), dtype=torch.int32, device=dev) for g in graphs]
         outs_l = [torch.empty((64, g.n), dtype=torch.int32, device=dev) for g in graphs]
         ms_batch = timed(lambda: gt.gt_bfs_batch(graphs, roots, outs_p, outs_l), 3)
+        work = gt.gt_bfs_batch_work(graphs[0])
+        bb = batch_bytes(work, [(len(r), g.n, g.stats()["n_core"]) for g, r in zip(graphs, roots)])
         lv = torch.empty(max(g.n for g in graphs), dtype=torch.int32, device=dev)
         pa = torch.empty_like(lv)
 
@@ -690,7 +692,11 @@ def batch_measure(a, gt, graphgen, torch, dev, parts, autotune) -> dict:
                       "batch_qps": round(nq / ms_batch * 1e3, 1), "sequential_qps": round(nq / ms_seq * 1e3, 1),
                       "batch_gteps_equiv": round(te / ms_batch / 1e6, 1),
                       "sequential_gteps_equiv": round(te / ms_seq / 1e6, 1),
-                      "speedup": round(ms_seq / ms_batch, 2)}
+                      "speedup": round(ms_seq / ms_batch, 2),
+                      "roofline": {"bound": "hbm", "kernel": "batched launch (batch_run + output passes)",
+                                   "achieved": round(bb / (ms_batch * 1e-3) / 1e9, 1), "peak": hbm_peak()[0],
+                                   "unit": "GB/s", "frac": round(bb / (ms_batch * 1e-3) / 1e9 / hbm_peak()[0], 4),
+                                   "bytes_per_launch": round(bb), "work": work}}
         del outs_p, outs_l
         for g in graphs:
             g.free()
@@ -704,10 +710,32 @@ def batch_measure(a, gt, graphgen, torch, dev, parts, autotune) -> dict:
     return res
 
 
+def batch_bytes(work: dict, graphs: list) -> float:
+    """Algorithmic bytes of one batched launch, per-unit figures of the lane-word method:
+    pull: 24 B per core vertex scanned (row-offset pair, visit word) + 12 B per adjacency
+    entry read (entry, frontier word of the neighbour); push: 12 B per entry read (entry,
+    visit word of the target); commit: 40 B per vertex discovered in a lane word (next
+    frontier word, visit word read and written, row-offset pair); output: 8 B per lane and
+    vertex written (level, parent) + 384 B per core vertex and lane word read (the staged
+    rows, 64 x (4 B parent + 2 B level)). graphs: (lanes, n, n_core) per graph."""
+    b = 24.0 * work["pull_vertices"] + 12.0 * work["pull_entries"] + 12.0 * work["push_entries"]
+    b += 40.0 * work["discovered"]
+    for lanes, n, nc in graphs:
+        b += 8.0 * lanes * n + 384.0 * nc * ((lanes + 63) // 64)
+    return b
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return json.load(open(path)).get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
 def batch_summary(res: dict) -> dict:
     return {"unit": "queries/s", "autotuned": True,
             "parts": {k: {x: v[x] for x in ("queries", "batch_qps", "sequential_qps", "batch_ms", "sequential_ms",
-                                            "speedup")} for k, v in res.items()},
+                                            "speedup", "roofline")} for k, v in res.items()},
             "how": "gt_bfs_batch (64-root lane words, one persistent launch, captured CUDA graph, autotuned) "
                    "against the same roots one gt_bfs call at a time; CUDA events, mean of 3 launches"}
 

@@ -173,6 +173,12 @@ GT_API int gt_bfs_plain(gt_graph_t g, int64_t root, int32_t* parent, int32_t* le
 GT_API int gt_bfs_batch(const gt_graph_t* graphs, int32_t ngraphs, const int64_t* roots,
                         const int32_t* roots_per_graph, int32_t* const* parent, int32_t* const* level,
                         void* stream);
+/* Work of the last gt_bfs_batch call whose first graph was g, summed over its lane words:
+ * out[0] adjacency entries read by bottom-up (pull) phases, out[1] adjacency entries read
+ * by top-down (push) phases, out[2] core vertices scanned by pull phases, out[3] vertices
+ * discovered (a vertex counts once per lane word and level that discovers it). For the
+ * algorithmic-bytes roofline of the batched launch. */
+GT_API int gt_bfs_batch_work(gt_graph_t g, int64_t* out);
 /* Failure detection of the batched launches (no counterpart in the paper). Every wait of
  * the persistent kernel at a grid barrier is bounded: after `polls` polls (default 2^26,
  * seconds) the waiting CTA raises an error flag, every CTA leaves the kernel, and the call

@@ -99,6 +99,7 @@ def lib():
                 "gt_serve_destroy": (ctypes.c_int, [p]),
                 "gt_count_traversed": (ctypes.c_int, [p, i64, p, i64, p, p]),
                 "gt_test_batch_barrier": (None, [ctypes.c_uint32, ctypes.c_uint32]),
+                "gt_bfs_batch_work": (ctypes.c_int, [p, p]),
                 "gt_strerror": (ctypes.c_char_p, [ctypes.c_int]),
                 "gt_last_error": (ctypes.c_char_p, []),
             }
@@ -404,6 +405,13 @@ class Server:
             self.destroy()
         except Exception:
             pass
+
+
+def gt_bfs_batch_work(g) -> dict:
+    """Work counts of the last gt_bfs_batch call led by graph g (see gt.h)."""
+    arr = (ctypes.c_int64 * 4)()
+    _check(lib().gt_bfs_batch_work(g._h, arr), "gt_bfs_batch_work")
+    return {"pull_entries": arr[0], "push_entries": arr[1], "pull_vertices": arr[2], "discovered": arr[3]}
 
 
 def gt_test_batch_barrier(polls: int = 0, extra: int = 0) -> None:

@@ -113,6 +113,9 @@ struct BatchCtl {
   int emit;            // slots with lanes to write at this level boundary
   unsigned int polls;  // a barrier wait gives up after this many polls
   unsigned int extra;  // arrivals a barrier waits for beyond the grid's (0; failure tests only)
+  // work of the launch: adjacency entries read by pull phases and by push phases, core
+  // vertices scanned by pull phases, vertices discovered (summed over lane words)
+  unsigned long long work[4];
 };
 
 // Barrier wait bounds of the batched launches (see gt_test_batch_barrier): the default
@@ -178,9 +181,10 @@ __device__ __forceinline__ void set_lane_levels(const SlotDev& s, int32_t w, uin
 // `want` not yet in `got` the first neighbour whose frontier word carries it (so the
 // smallest). Four entries and their frontier words are loaded together per step.
 __device__ __forceinline__ uint64_t hits_thread(const SlotDev& s, const uint64_t* __restrict__ fc, int32_t w,
-                                                uint64_t want, uint64_t got, int64_t b, int64_t e) {
+                                                uint64_t want, uint64_t got, int64_t b, int64_t e, int64_t& ne) {
   int32_t* prow = s.P + (int64_t)w * 64;
-  for (int64_t k = b; k < e && got != want; k += 4) {
+  int64_t k = b;
+  for (; k < e && got != want; k += 4) {
     int32_t u[4];
     uint64_t f[4];
 #pragma unroll
@@ -201,6 +205,7 @@ __device__ __forceinline__ uint64_t hits_thread(const SlotDev& s, const uint64_t
       }
     }
   }
+  ne += min(k, e) - b;
   return got;
 }
 
@@ -210,10 +215,11 @@ __device__ __forceinline__ uint64_t hits_thread(const SlotDev& s, const uint64_t
 // taken with atomicMin (ascending entries = ascending ids: the smallest chunk wins).
 template <bool ATOMIC>
 __device__ __forceinline__ uint64_t hits_warp(const SlotDev& s, const uint64_t* __restrict__ fc, int32_t w,
-                                              uint64_t want, uint64_t got, int64_t b, int64_t e) {
+                                              uint64_t want, uint64_t got, int64_t b, int64_t e, int64_t& ne) {
   const int lane = threadIdx.x & 31;
   int32_t* prow = s.P + (int64_t)w * 64;
-  for (int64_t k0 = b; k0 < e && got != want; k0 += 32 * CW) {
+  int64_t k0 = b;
+  for (; k0 < e && got != want; k0 += 32 * CW) {
     int32_t u[CW];
     uint64_t h[CW];
 #pragma unroll
@@ -249,6 +255,7 @@ __device__ __forceinline__ uint64_t hits_warp(const SlotDev& s, const uint64_t* 
       got |= __shfl_sync(FULL, incl, 31);
     }
   }
+  if (lane == 0) ne += min(k0, e) - b;
   return got;
 }
 
@@ -268,8 +275,9 @@ __device__ __forceinline__ void list_append(bool first, int32_t w, int64_t* coun
 // next word (the first to give it any lists it) and, per lane, the smallest frontier
 // neighbour as parent by atomicMin.
 __device__ __forceinline__ void td_push(const SlotDev& s, uint64_t f, int32_t vo, int64_t b, int64_t e,
-                                        uint64_t* fn, int64_t* count, int32_t* list) {
+                                        uint64_t* fn, int64_t* count, int32_t* list, int64_t& ne) {
   const int lane = threadIdx.x & 31;
+  if (lane == 0) ne += max(e - b, (int64_t)0);
   for (int64_t k0 = b; k0 < e; k0 += 32 * CW) {
     int32_t w[CW];
     uint64_t vis[CW];
@@ -454,6 +462,7 @@ __global__ void __launch_bounds__(BT)
   const int lane = threadIdx.x & 31;
   const int64_t gw = gtid() >> 5, nw = gthreads() >> 5;
   unsigned int gen = 0;
+  int64_t w_pull = 0, w_push = 0, v_pull = 0, v_disc = 0;  // work of this thread (see BatchCtl)
   for (int iter_guard = 0; iter_guard < 65534; ++iter_guard) {
     // snapshot of the per-slot control words for this level
     for (int i = threadIdx.x; i < nslots; i += BT) {
@@ -484,7 +493,7 @@ __global__ void __launch_bounds__(BT)
                 atomicAdd((unsigned long long*)&sctl[si].q_n, (unsigned long long)(nch - 1));
             for (int64_t c = 1; c < nch; ++c) s.q[p + c - 1] = ((uint64_t)v << 32) | (uint32_t)c;
           }
-          td_push(s, fc[v], s.new2old[v], b, min(e, b + BATCH_CHUNK), fn, &sctl[si].fl_n[nxt], s.fl[nxt]);
+          td_push(s, fc[v], s.new2old[v], b, min(e, b + BATCH_CHUNK), fn, &sctl[si].fl_n[nxt], s.fl[nxt], w_push);
         }
       } else {
         // pull: every core vertex still missing lanes scans its ascending adjacency for the
@@ -501,7 +510,10 @@ __global__ void __launch_bounds__(BT)
           if (i < s.n_lanes) {
             w = s.lanes[i];
             const uint64_t miss = act & ~s.visit[w];
-            if (miss) got = hits_thread(s, fc, w, miss, 0ull, s.crow[w], s.crow[w + 1]);
+            if (miss) {
+              got = hits_thread(s, fc, w, miss, 0ull, s.crow[w], s.crow[w + 1], w_pull);
+              ++v_pull;
+            }
           }
           bool first = got != 0;
           if (got) {
@@ -520,8 +532,9 @@ __global__ void __launch_bounds__(BT)
           const int64_t rb = s.crow[w], re = s.crow[w + 1];
           const int64_t b = rb + (int64_t)(uint32_t)item * BATCH_CHUNK, e = min(re, b + BATCH_CHUNK);
           const bool whole = b == rb && e == re;
-          const uint64_t got = whole ? hits_warp<false>(s, fc, w, miss, 0ull, b, e)
-                                     : hits_warp<true>(s, fc, w, miss, 0ull, b, e);
+          if (lane == 0 && b == rb) ++v_pull;
+          const uint64_t got = whole ? hits_warp<false>(s, fc, w, miss, 0ull, b, e, w_pull)
+                                     : hits_warp<true>(s, fc, w, miss, 0ull, b, e, w_pull);
           bool first = false;
           if (got && lane == 0) {
             if (whole && !yg) {
@@ -558,7 +571,8 @@ __global__ void __launch_bounds__(BT)
                     atomicAdd((unsigned long long*)&sctl[si].q_n, (unsigned long long)(nch - 1));
                 for (int64_t c = 1; c < nch; ++c) s.q[p + c - 1] = ((uint64_t)vv << 32) | (uint32_t)c;
               }
-              td_push(s, ff, s.new2old[vv], b, min(e, b + BATCH_CHUNK), fn, &sctl[si].fl_n[nxt], s.fl[nxt]);
+              td_push(s, ff, s.new2old[vv], b, min(e, b + BATCH_CHUNK), fn, &sctl[si].fl_n[nxt], s.fl[nxt],
+                      w_push);
             }
           }
         }
@@ -582,7 +596,7 @@ __global__ void __launch_bounds__(BT)
         const int64_t rb = s.crow[v], re = s.crow[v + 1];
         const int64_t b = rb + (int64_t)(uint32_t)item * BATCH_CHUNK;
         td_push(s, s.front[cur][v] & lanes, s.new2old[v], b, min(re, b + BATCH_CHUNK), s.front[nxt],
-                &sctl[si].fl_n[nxt], s.fl[nxt]);
+                &sctl[si].fl_n[nxt], s.fl[nxt], w_push);
       }
     }
     if (any_q && !grid_barrier(bc, gen)) return;
@@ -597,6 +611,7 @@ __global__ void __launch_bounds__(BT)
       int64_t msum = 0;
       uint64_t alive = 0;
       for (int64_t j = gtid(); j < nn; j += gthreads()) {
+        ++v_disc;
         const int32_t w = s.fl[nxt][j];
         const uint64_t nb = fn[w];
         msum += s.crow[w + 1] - s.crow[w];
@@ -669,7 +684,18 @@ __global__ void __launch_bounds__(BT)
     }
     if (!grid_barrier(bc, gen)) return;
     if (early && *(volatile int*)&bc->emit && !emit_lanes(slots, sctl, nslots, bc, segs, maxh, gen)) return;
-    if (*(volatile int*)&bc->live <= 0) return;
+    if (*(volatile int*)&bc->live <= 0) break;
+  }
+  // the launch's work counts: warp sums, one atomic per warp and counter
+  w_pull = warp_sum(w_pull);
+  w_push = warp_sum(w_push);
+  v_pull = warp_sum(v_pull);
+  v_disc = warp_sum(v_disc);
+  if (lane == 0) {
+    if (w_pull) atomicAdd(&bc->work[0], (unsigned long long)w_pull);
+    if (w_push) atomicAdd(&bc->work[1], (unsigned long long)w_push);
+    if (v_pull) atomicAdd(&bc->work[2], (unsigned long long)v_pull);
+    if (v_disc) atomicAdd(&bc->work[3], (unsigned long long)v_disc);
   }
 }
 
@@ -920,6 +946,7 @@ void enqueue_batch(SlotDev* d_slots, SlotCtl* d_ctl, BatchCtl* d_bc, ResolveSeg*
   batch_fixup<<<ns, 64, 0, st>>>(d_slots, ns);
   for (int h = 0; h < maxh; ++h) batch_resolve<<<dim3(64, ns), BT, 0, st>>>(d_slots, d_seg + (size_t)h * ns, ns);
   cudaMemcpyAsync(h_err, &d_bc->err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(h_err + 4, d_bc->work, sizeof(d_bc->work), cudaMemcpyDeviceToHost, st);
 }
 
 }  // namespace
@@ -953,7 +980,8 @@ int batch_launch(BatchCtx* ctx, const SlotSpec* specs, int nspecs, int sm_share,
     ctx->cap_bytes = bytes;
   }
   if (!ctx->h_err) {
-    int rc = cuda_fail(cudaHostAlloc((void**)&ctx->h_err, sizeof(int) * 4, cudaHostAllocDefault), "pinned status");
+    // status word, then (from int 4 on) the launch's four work counters
+    int rc = cuda_fail(cudaHostAlloc((void**)&ctx->h_err, sizeof(int) * 12, cudaHostAllocDefault), "pinned status");
     if (rc) return rc;
   }
   ctx->h_err[0] = 0;
@@ -1018,7 +1046,7 @@ int batch_launch(BatchCtx* ctx, const SlotSpec* specs, int nspecs, int sm_share,
       hseg[(size_t)h * ns + i] = sg;
     }
   }
-  *hbc = BatchCtl{0u, 0, ns, 0, g_barrier_polls.load(), g_barrier_extra.load()};
+  *hbc = BatchCtl{0u, 0, ns, 0, g_barrier_polls.load(), g_barrier_extra.load(), {0ull, 0ull, 0ull, 0ull}};
   char* base = (char*)ctx->dev;
   SlotDev* d_slots = (SlotDev*)base;
   SlotCtl* d_ctl = (SlotCtl*)(base + t_slots);
@@ -1134,6 +1162,7 @@ int run_batch(gt_graph* const* graphs, int ngraphs, const int64_t* roots, const 
   int rc = batch_launch(g0->batch_ctx, specs.data(), (int)specs.size(), 0, st);
   if (!rc) rc = cuda_fail(cudaStreamSynchronize(st), "batch sync");
   if (!rc) rc = batch_status(g0->batch_ctx);
+  if (!rc) memcpy(g0->batch_work, g0->batch_ctx->h_err + 4, sizeof(g0->batch_work));
   return rc;
 }
 

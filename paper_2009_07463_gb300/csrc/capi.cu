@@ -392,6 +392,15 @@ GT_API int gt_bfs_roots(gt_graph_t g, const int64_t* roots, int32_t k, int32_t* 
 
 GT_API void gt_test_batch_barrier(uint32_t polls, uint32_t extra) { set_barrier_test(polls, extra); }
 
+GT_API int gt_bfs_batch_work(gt_graph_t g, int64_t* out) {
+  if (!g || !out) {
+    set_error("gt_bfs_batch_work: null argument");
+    return GT_EINVAL;
+  }
+  for (int i = 0; i < 4; ++i) out[i] = g->batch_work[i];
+  return GT_OK;
+}
+
 GT_API int gt_bfs_plain(gt_graph_t g, int64_t root, int32_t* parent, int32_t* level, void* stream) {
   return bfs_common(g, false, root, parent, level, stream);
 }

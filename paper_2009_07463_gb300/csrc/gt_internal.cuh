@@ -154,6 +154,7 @@ struct gt_graph {
   std::vector<void*> batch_mem;
   int batch_slots_alloc = 0;
   gt::BatchCtx* batch_ctx = nullptr;
+  int64_t batch_work[4] = {0, 0, 0, 0};  // work counts of the last gt_bfs_batch led by this graph
   int64_t device_bytes = 0;
 };
 

@@ -19,6 +19,15 @@ def test_byte_models_follow_the_per_unit_figures():
     assert bench.td_bytes({"frontier": 3, "frontier_edges": 50, "discovered": 7}) == 16 * 3 + 8 * 50 + 12 * 7
 
 
+def test_batch_byte_model_follows_the_per_unit_figures():
+    work = {"pull_vertices": 10, "pull_entries": 100, "push_entries": 50, "discovered": 7}
+    # one graph with 64 lanes, 1000 vertices, 400 core vertices (one lane word)
+    assert bench.batch_bytes(work, [(64, 1000, 400)]) == pytest.approx(
+        24 * 10 + 12 * 100 + 12 * 50 + 40 * 7 + 8 * 64 * 1000 + 384 * 400)
+    # 65 lanes take two lane words
+    assert bench.batch_bytes({k: 0 for k in work}, [(65, 10, 4)]) == pytest.approx(8 * 65 * 10 + 384 * 4 * 2)
+
+
 def test_launch_count_per_traversal():
     # reset, start, anchors, output, fixup + per level one decide and the step kernels
     # (top-down 1, plus a queue rebuild after bottom-up; bottom-up gather + scan, or one

@@ -187,3 +187,25 @@ def test_batch_same_graph_twice(torch):
     P, L = run_batch(torch, [g, g], [r1, r2])
     check_rows(P[0], L[0], og, r1, "first list")
     check_rows(P[1], L[1], og, r2, "second list")
+
+
+def test_batch_work_counts(torch):
+    """The launch's work counts (the batched roofline's inputs): with one root in the lane
+    word every reached core vertex but the start is discovered exactly once; with 64 roots
+    the pull and push phases both read adjacency entries."""
+    n = 1 << 14
+    e = graphgen.rmat_edges(14, 16, seed=27)
+    og = OracleGraph(e, n)
+    g = gt.gt_graph_build(e, n)
+    core = np.isin(g.vertex_type(), [0, 1])  # CI, CE
+    deg = og.degree()
+    r = int(np.flatnonzero(core & (deg > 2))[0])
+    (P,), (L,) = run_batch(torch, [g], [[r]])
+    lv = L[0]
+    w = gt.gt_bfs_batch_work(g)
+    assert w["discovered"] == int((core & (lv >= 0)).sum()) - 1
+    roots = graphgen.pick_roots(28, n, 64, deg).tolist()
+    run_batch(torch, [g], [roots])
+    w = gt.gt_bfs_batch_work(g)
+    assert w["pull_entries"] > 0 and w["push_entries"] > 0 and w["pull_vertices"] > 0
+    assert w["discovered"] >= int(core.sum() * 0.5)
