@@ -59,6 +59,10 @@ def parse():
     ap.add_argument("--trace-out", default="")
     ap.add_argument("--bu-hub-first", action="store_true",
                     help="degree-aware bottom-up (Alg. 3 probe order, min-id parents restored after the loop)")
+    ap.add_argument("--alpha", type=int, default=0, help="top-down -> bottom-up switch constant (0: library default)")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="build without the unsplit view (with --no-extras: less device memory, e.g. for profiling)")
+    ap.add_argument("--root-list", default="", help="comma-separated roots instead of the seeded ones")
     ap.add_argument("--launch-mode", default="graph", choices=["graph", "host"],
                     help="host: one launch per kernel (lets ncu see every kernel; slower)")
     ap.add_argument("--workload", default="et", choices=["et", "batch", "serve", "study"],
@@ -351,17 +355,21 @@ def main():
     graphgen.rmat_edges_device(edges.data_ptr(), a.scale, m, seed=a.seed, stream=stream.cuda_stream)
     torch.cuda.synchronize()
     t0 = time.time()
-    g = gt.gt_graph_build(edges, n, mh=a.mh, stream=stream)
+    g = gt.gt_graph_build(edges, n, mh=a.mh, keep_plain=not (a.no_plain and a.no_extras), stream=stream)
     torch.cuda.synchronize()
     build_s = time.time() - t0
     if a.launch_mode == "host":
         g.set_tuning(launch_mode=1)
+    if a.alpha > 0:
+        g.set_tuning(alpha=a.alpha)
     if a.bu_hub_first:
         g.set_tuning(bu_hub_first=1)
     st = g.stats()
     deg = g.degree()
     all_roots = graphgen.pick_roots(a.root_seed, n, a.roots * world, deg)
     roots = rank_roots(all_roots, rank, a.roots)
+    if a.root_list:
+        roots = [int(x) for x in a.root_list.split(",") if x]
 
     parent = torch.empty(n, dtype=torch.int32, device=dev)
     level = torch.empty(n, dtype=torch.int32, device=dev)
@@ -521,7 +529,8 @@ def main():
         bu_gbs = bu_b / (bu_t * 1e-3) / 1e9 if bu_t > 0 else 0.0
         td_gbs = td_b / (td_t * 1e-3) / 1e9 if td_t > 0 else 0.0
         trf = traffic_from_profiles("bfs_bu")
-        out["roofline"] = {"bound": "hbm", "kernel": "bfs_bu_gather+bfs_bu_scan", "achieved": round(bu_gbs, 1), "peak": peak,
+        out["roofline"] = {"bound": "hbm", "kernel": "bottom-up step (bfs_mark, bfs_bu_stream; bfs_bu_gather + bfs_bu_scan)",
+                           "achieved": round(bu_gbs, 1), "peak": peak,
                            "peak_source": peak_src, "unit": "GB/s", "frac": round(bu_gbs / peak, 4),
                            "peak_nominal": HBM_NOMINAL_GBS, "frac_nominal": round(bu_gbs / HBM_NOMINAL_GBS, 4),
                            "traffic": trf, "launches": bu_n,
