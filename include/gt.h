@@ -104,7 +104,8 @@ typedef struct gt_level_info {
   int32_t level;        /* level of the frontier this step expanded */
   int32_t direction;    /* 0 top-down, 1 bottom-up over the gathered list of unvisited
                            vertices, 2 bottom-up streaming over all vertices (used while
-                           most vertices are unvisited) */
+                           more than a sixth of them are unvisited), 3 the same with a
+                           shared-memory filter of a small frontier (after a top-down step) */
   int64_t frontier;     /* frontier vertices n_f */
   int64_t frontier_edges; /* sum of their degrees m_f */
   int64_t unvisited_edges; /* m_u before the step */

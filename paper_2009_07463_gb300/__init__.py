@@ -271,7 +271,8 @@ class Graph:
         out = []
         for i in range(min(nl.value, cap)):
             t = arr[i]
-            out.append({"level": t.level, "direction": "bu" if t.direction else "td", "stream": t.direction == 2,
+            out.append({"level": t.level, "direction": "bu" if t.direction else "td", "stream": t.direction >= 2,
+                        "filtered": t.direction == 3,
                         "frontier": t.frontier,
                         "frontier_edges": t.frontier_edges, "unvisited_edges": t.unvisited_edges,
                         "discovered": t.discovered, "examined": t.examined, "step_ms": t.step_ms})

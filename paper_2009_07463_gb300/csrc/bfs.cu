@@ -999,7 +999,7 @@ __global__ void bfs_decide(BfsArgs a, cudaGraphConditionalHandle h_loop, cudaGra
     if (c->nlevels < MAX_TRACE) {
       gt_level_info& t = c->trace[c->nlevels];
       t.level = L;
-      t.direction = (dir == DIR_BU && c->bu_stream) ? 2 : dir;
+      t.direction = (dir == DIR_BU && c->bu_stream) ? (c->bu_bloom ? 3 : 2) : dir;
       t.frontier = c->n_f;
       t.frontier_edges = c->m_f;
       t.unvisited_edges = c->m_u;

@@ -223,6 +223,29 @@ def test_trace_directions(torch_cuda):
     assert {t["direction"] for t in g.trace()} == {"td"}
 
 
+def test_filtered_bottom_up_levels(torch_cuda):
+    """Roots whose first bottom-up level follows a top-down level with a small frontier run
+    the filtered streaming step (trace direction 3); their answers equal the oracle's, and so
+    do the same roots with the filter never taken (all bottom-up from the start)."""
+    torch = torch_cuda
+    n = 1 << 18
+    e = graphgen.rmat_edges(18, 16, seed=41)
+    og = OracleGraph(e, n)
+    g = gt.gt_graph_build(e, n)
+    roots = graphgen.pick_roots(42, n, 24, og.degree()).tolist()
+    want = oracle_many(og, roots)
+    filtered = 0
+    for r, w in zip(roots, want):
+        for plain in (False, True):
+            assert_same(bfs_dev(torch, g, r, plain), w, f"root {r} plain={plain}")
+            filtered += any(t["filtered"] for t in g.trace())
+    assert filtered > 0, "no traversal took the filtered bottom-up step"
+    g.set_tuning(force_direction=2)
+    for r, w in zip(roots[:6], want[:6]):
+        assert_same(bfs_dev(torch, g, r), w, f"all bottom-up root {r}")
+        assert not any(t["filtered"] for t in g.trace())
+
+
 def test_host_output_buffers(torch_cuda):
     torch = torch_cuda
     n = 1 << 13
