@@ -43,6 +43,7 @@ extern "C" {
 #define GT_EBUSY (-4)    /* resource in use */
 #define GT_EDEVICE (-5)  /* CUDA error (detail in gt_last_error) */
 #define GT_ENOTSUP (-6)  /* not supported on this device / build */
+#define GT_EIO (-7)      /* a file could not be read or written, or is not a saved graph */
 
 /* Vertex classes of Sec. 4.2 (codes of gt_graph_vertex_type). */
 #define GT_CORE_INTERNAL 0 /* CI */
@@ -131,6 +132,17 @@ GT_API void gt_tuning_default(gt_tuning* t);
 GT_API int gt_graph_build(const int64_t* edges, int64_t m, int64_t n, const gt_config* cfg, void* stream,
                           gt_graph_t* out);
 GT_API void gt_graph_free(gt_graph_t g);
+/* Checkpoint of a built graph (no counterpart in the paper): gt_graph_save writes what the
+ * build derived from the tuples (CSR, Alg. 8 classes and tree parents, core relabel and
+ * core CSR, edge-tree lists, batched work lists, configuration, tuning and statistics) to
+ * the file at `path`; gt_graph_load reads such a file into a new handle on the current
+ * device (or the device of `stream`), allocating the per-traversal state as a build does,
+ * so the graph need not be rebuilt from its tuples. Both synchronise `stream`. GT_EINVAL
+ * for a null argument, GT_EIO if the file cannot be written or read, is truncated or was
+ * not written by this version (a failed save removes the file; a failed load keeps
+ * nothing), GT_ENOMEM if device memory runs out. */
+GT_API int gt_graph_save(gt_graph_t g, const char* path, void* stream);
+GT_API int gt_graph_load(const char* path, void* stream, gt_graph_t* out);
 GT_API int gt_graph_stats(gt_graph_t g, gt_stats* out);
 /* Copy Alg. 8's vertex_type[n] (GT_* class codes) into out (host or device). */
 GT_API int gt_graph_vertex_type(gt_graph_t g, uint8_t* out, void* stream);
@@ -189,6 +201,12 @@ GT_API int gt_bfs_batch_work(gt_graph_t g, int64_t* out);
  * launch gives up at its first barrier after `polls` polls. polls = 0, extra = 0 restores
  * the default. Process-wide; not for use while other threads launch batches. */
 GT_API void gt_test_batch_barrier(uint32_t polls, uint32_t extra);
+/* Allocation-failure injection for tests (no counterpart in the paper): once `after` more
+ * device allocations of graph construction (the handle's arrays and the build's
+ * temporaries) have succeeded, the next one fails as if device memory had run out, so
+ * gt_graph_build returns GT_ENOMEM and frees what it had allocated; after < 0 disables
+ * it. Process-wide; not for use while other threads build graphs. */
+GT_API void gt_test_fail_alloc(int32_t after);
 /* Autotuner: times edge-tree BFS from nsample seeded roots of degree >= 1 (and one batch
  * of up to 64 of them) under settings of gt_tuning, walking one parameter at a time, and
  * keeps the fastest in the handle (also copied to *best if non-null). Results do not

@@ -15,7 +15,7 @@ import numpy as np
 
 from . import native
 
-GT_OK, GT_EINVAL, GT_ENOMEM, GT_ETIMEOUT, GT_EBUSY, GT_EDEVICE, GT_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+GT_OK, GT_EINVAL, GT_ENOMEM, GT_ETIMEOUT, GT_EBUSY, GT_EDEVICE, GT_ENOTSUP, GT_EIO = 0, -1, -2, -3, -4, -5, -6, -7
 GT_SERVE_ADAPTIVE, GT_SERVE_BATCHED, GT_SERVE_SINGLE = 0, 1, 2
 CORE_INTERNAL, CORE_EDGE, TREE_INTERNAL, TREE_LEAF, VERTEX_ZERO = 0, 1, 2, 3, 4
 
@@ -100,6 +100,9 @@ def lib():
                 "gt_count_traversed": (ctypes.c_int, [p, i64, p, i64, p, p]),
                 "gt_test_batch_barrier": (None, [ctypes.c_uint32, ctypes.c_uint32]),
                 "gt_bfs_batch_work": (ctypes.c_int, [p, p]),
+                "gt_test_fail_alloc": (None, [i32]),
+                "gt_graph_save": (ctypes.c_int, [p, ctypes.c_char_p, p]),
+                "gt_graph_load": (ctypes.c_int, [ctypes.c_char_p, p, p]),
                 "gt_strerror": (ctypes.c_char_p, [ctypes.c_int]),
                 "gt_last_error": (ctypes.c_char_p, []),
             }
@@ -290,6 +293,20 @@ def gt_graph_build(edges, n: int, mh: int = 0, keep_plain: bool = True, stream=N
     return Graph(h.value, int(n))
 
 
+def gt_graph_save(g: Graph, path: str, stream=None) -> None:
+    """Write the built graph to `path` (gt_graph_load reads it back)."""
+    _check(lib().gt_graph_save(g._h, os.fsencode(path), _stream(stream)), "gt_graph_save")
+
+
+def gt_graph_load(path: str, stream=None) -> Graph:
+    """A graph handle from a file written by gt_graph_save."""
+    h = ctypes.c_void_p()
+    _check(lib().gt_graph_load(os.fsencode(path), _stream(stream), ctypes.byref(h)), "gt_graph_load")
+    g = Graph(h.value, 0)
+    g.n = int(g.stats()["n"])
+    return g
+
+
 def gt_graph_free(g: Graph):
     g.free()
 
@@ -413,6 +430,12 @@ def gt_bfs_batch_work(g) -> dict:
     arr = (ctypes.c_int64 * 4)()
     _check(lib().gt_bfs_batch_work(g._h, arr), "gt_bfs_batch_work")
     return {"pull_entries": arr[0], "push_entries": arr[1], "pull_vertices": arr[2], "discovered": arr[3]}
+
+
+def gt_test_fail_alloc(after: int = -1) -> None:
+    """Allocation-failure injection for tests: the device allocation of graph construction
+    after `after` more successful ones fails (GT_ENOMEM); -1 disables it."""
+    lib().gt_test_fail_alloc(int(after))
 
 
 def gt_test_batch_barrier(polls: int = 0, extra: int = 0) -> None:

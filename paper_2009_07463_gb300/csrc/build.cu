@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "gt_device.cuh"
@@ -371,8 +372,27 @@ int bits_for(int64_t n) {
 // used), so a kernel may read them as aligned vectors.
 int64_t col_alloc(int64_t nnz) { return (std::max<int64_t>(nnz, 1) + 3) / 4 * 4; }
 
+// Allocation-failure injection for tests (gt_test_fail_alloc): once `after` more graph
+// allocations have succeeded, the next one fails as if device memory had run out.
+std::atomic<int> g_fail_after{-1};
+
+static bool injected_alloc_failure() {
+  int k = g_fail_after.load();
+  while (k >= 0) {
+    if (g_fail_after.compare_exchange_weak(k, k - 1)) return k == 0;
+  }
+  return false;
+}
+
+void set_alloc_test(int after) { g_fail_after.store(after < 0 ? -1 : after); }
+
 int device_malloc(gt_graph* g, void** p, size_t bytes) {
   if (bytes == 0) bytes = 16;
+  if (injected_alloc_failure()) {
+    *p = nullptr;
+    set_error("device allocation failed (injected by gt_test_fail_alloc)");
+    return GT_ENOMEM;
+  }
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -510,6 +530,11 @@ struct Temps {
 
 static int tmp_malloc(Temps& t, void** p, size_t bytes) {
   if (bytes == 0) bytes = 16;
+  if (injected_alloc_failure()) {
+    *p = nullptr;
+    set_error("device allocation failed (build temporary; injected by gt_test_fail_alloc)");
+    return GT_ENOMEM;
+  }
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();

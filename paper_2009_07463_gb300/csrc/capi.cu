@@ -390,7 +390,70 @@ GT_API int gt_bfs_roots(gt_graph_t g, const int64_t* roots, int32_t k, int32_t* 
   return bfs_roots(g, roots, k, parent, level, (cudaStream_t)stream);
 }
 
+GT_API int gt_graph_save(gt_graph_t g, const char* path, void* stream) {
+  if (!g || !path) {
+    set_error("gt_graph_save: null argument");
+    return GT_EINVAL;
+  }
+  int rc = cuda_fail(cudaSetDevice(g->device), "cudaSetDevice");
+  if (rc) return rc;
+  FILE* f = fopen(path, "wb");
+  if (!f) {
+    set_error(std::string("gt_graph_save: cannot open ") + path + " for writing");
+    return GT_EIO;
+  }
+  rc = save_graph(g, f, (cudaStream_t)stream);
+  if (fclose(f) != 0 && rc == GT_OK) {
+    set_error("gt_graph_save: write failed");
+    rc = GT_EIO;
+  }
+  if (rc) remove(path);
+  return rc;
+}
+
+GT_API int gt_graph_load(const char* path, void* stream, gt_graph_t* out) {
+  if (!path || !out) {
+    set_error("gt_graph_load: null argument");
+    return GT_EINVAL;
+  }
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0;
+  int rc = select_device(s, &dev);
+  if (rc) return rc;
+  FILE* f = fopen(path, "rb");
+  if (!f) {
+    set_error(std::string("gt_graph_load: cannot open ") + path);
+    return GT_EIO;
+  }
+  gt_graph* g = new (std::nothrow) gt_graph();
+  if (!g) {
+    fclose(f);
+    return GT_ENOMEM;
+  }
+  g->device = dev;
+  gt_config_default(&g->cfg);
+  gt_tuning_default(&g->tuning);
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  g->launch.sms = sms > 0 ? sms : 1;
+  rc = load_graph(g, f, s);
+  fclose(f);
+  if (rc) {
+    cudaStreamSynchronize(s);
+    cudaGetLastError();
+    free_graph(g);
+    delete g;
+    return rc;
+  }
+  apply_launch(g);
+  *out = g;
+  return GT_OK;
+}
+
 GT_API void gt_test_batch_barrier(uint32_t polls, uint32_t extra) { set_barrier_test(polls, extra); }
+
+GT_API void gt_test_fail_alloc(int32_t after) { set_alloc_test(after); }
 
 GT_API int gt_bfs_batch_work(gt_graph_t g, int64_t* out) {
   if (!g || !out) {
@@ -514,6 +577,7 @@ GT_API const char* gt_strerror(int code) {
     case GT_EBUSY: return "busy";
     case GT_EDEVICE: return "CUDA error";
     case GT_ENOTSUP: return "not supported";
+    case GT_EIO: return "file error";
     default: return "unknown error";
   }
 }

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
 
 #include <string>
 #include <vector>
@@ -170,6 +171,15 @@ int alloc_view_state(gt_graph* g, View& v, cudaStream_t s);
 int ensure_hub(gt_graph* g, View& v, cudaStream_t s);
 void free_graph(gt_graph* g);
 int device_malloc(gt_graph* g, void** p, size_t bytes);
+// Allocation-failure injection (tests): the allocation after `after` more successful ones
+// fails with GT_ENOMEM; after < 0 disables it.
+void set_alloc_test(int after);
+// Entries a column array of nnz entries is allocated with (whole 16-byte pieces).
+int64_t col_alloc(int64_t nnz);
+
+// persist.cu: a built graph to an open file and back (see gt_graph_save / gt_graph_load)
+int save_graph(const gt_graph* g, FILE* f, cudaStream_t s);
+int load_graph(gt_graph* g, FILE* f, cudaStream_t s);
 
 // scan.cu
 // out[i] = sum_{j < i} in[j] for i in [0, n]; out has n + 1 entries.

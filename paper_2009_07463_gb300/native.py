@@ -17,7 +17,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libgt.so")
 ARCH = "sm_103a"
 
-SOURCES = ["scan.cu", "radix.cu", "build.cu", "bfs.cu", "batch.cu", "tune.cu", "serve.cu", "capi.cu"]
+SOURCES = ["scan.cu", "radix.cu", "build.cu", "bfs.cu", "batch.cu", "tune.cu", "serve.cu", "persist.cu", "capi.cu"]
 
 
 def _deps() -> list[str]:
