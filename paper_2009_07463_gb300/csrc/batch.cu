@@ -14,7 +14,8 @@
 //               lane's parent (so min-id); short adjacencies a lane each, long ones in
 //               chunks a warp each, chunk results merged by atomicMin.
 //   E2 queued   every warp takes queued top-down chunks (only when some slot queued any).
-//   P  commit   every reached lane gets its level; visit |= new lanes.
+//   P  commit   every reached lane gets its level; visit |= new lanes (vertices a pull
+//               scanned whole are committed by that pull already, without a mailbox).
 //   D  decide   clear the old frontier words, swap, pick the next direction per slot.
 // Per lane the levels and parents equal those of a single-root gt_bfs (Alg. 9): each
 // lane is an ordinary BFS from its root's core vertex, levels are shared iterations, and
@@ -40,6 +41,15 @@ namespace {
 constexpr int BT = 256;
 constexpr int MAX_SLOTS_SMEM = 256;
 constexpr int CW = 4;  // 32-entry windows a warp keeps in flight on one adjacency
+
+// What a level reads once (adjacency entries a warp scans, the work lists, the visit words
+// of the vertices it pulls) is loaded evict-first, so that L2 keeps the frontier words that
+// the pull gathers at random (8 B per core vertex: 54 MB at R-MAT scale 24). A lane's short
+// adjacency (16 B per step from one or two 128 B lines) stays on plain loads: evict-first
+// ones measured 0.7 % slower at scale 24.
+#define BATCH_STREAM_LD(p) __ldcs(p)
+
+constexpr bool FUSE_COMMIT = true;  // pulls commit the vertices they scan whole
 
 struct LaneInit {
   int32_t start;    // core id the lane's BFS starts from (-1: nothing to traverse)
@@ -160,21 +170,24 @@ __device__ bool grid_barrier(BatchCtl* bc, unsigned int& gen) {
 
 // Sets level `it` for the lanes in `lanes` of w's staged row: per group of 8 lanes (16 B)
 // one vector read-modify-write instead of one 2-byte store per lane.
-__device__ __forceinline__ void set_lane_levels(const SlotDev& s, int32_t w, uint64_t lanes, uint16_t it) {
+// Group q (lanes 8q .. 8q+7) of that update.
+__device__ __forceinline__ void set_lane_levels_q(const SlotDev& s, int32_t w, uint64_t lanes, uint16_t it, int q) {
+  const uint32_t m8 = (uint32_t)(lanes >> (8 * q)) & 0xFFu;
+  if (!m8) return;
   uint4* row = reinterpret_cast<uint4*>(s.L + (int64_t)w * 64);
   const uint32_t it2 = (uint32_t)it * 0x10001u;
-  for (int q = 0; q < 8; ++q) {
-    const uint32_t m8 = (uint32_t)(lanes >> (8 * q)) & 0xFFu;
-    if (!m8) continue;
-    uint4 x = m8 == 0xFFu ? make_uint4(0, 0, 0, 0) : row[q];
-    uint32_t* xw = reinterpret_cast<uint32_t*>(&x);
+  uint4 x = m8 == 0xFFu ? make_uint4(0, 0, 0, 0) : row[q];
+  uint32_t* xw = reinterpret_cast<uint32_t*>(&x);
 #pragma unroll
-    for (int h = 0; h < 4; ++h) {
-      const uint32_t keep = ((m8 >> (2 * h)) & 1u ? 0u : 0xFFFFu) | ((m8 >> (2 * h + 1)) & 1u ? 0u : 0xFFFF0000u);
-      xw[h] = (xw[h] & keep) | (it2 & ~keep);
-    }
-    row[q] = x;
+  for (int h = 0; h < 4; ++h) {
+    const uint32_t keep = ((m8 >> (2 * h)) & 1u ? 0u : 0xFFFFu) | ((m8 >> (2 * h + 1)) & 1u ? 0u : 0xFFFF0000u);
+    xw[h] = (xw[h] & keep) | (it2 & ~keep);
   }
+  row[q] = x;
+}
+
+__device__ __forceinline__ void set_lane_levels(const SlotDev& s, int32_t w, uint64_t lanes, uint16_t it) {
+  for (int q = 0; q < 8; ++q) set_lane_levels_q(s, w, lanes, it, q);
 }
 
 // Ascending scan of entries [b, e) of w's adjacency by one thread, assigning each lane of
@@ -225,7 +238,7 @@ __device__ __forceinline__ uint64_t hits_warp(const SlotDev& s, const uint64_t* 
 #pragma unroll
     for (int t = 0; t < CW; ++t) {
       const int64_t k = k0 + 32 * t + lane;
-      u[t] = k < e ? s.ccol[k] : -1;
+      u[t] = k < e ? BATCH_STREAM_LD(&s.ccol[k]) : -1;
     }
 #pragma unroll
     for (int t = 0; t < CW; ++t) h[t] = u[t] >= 0 ? fc[u[t]] & want : 0ull;
@@ -284,7 +297,7 @@ __device__ __forceinline__ void td_push(const SlotDev& s, uint64_t f, int32_t vo
 #pragma unroll
     for (int t = 0; t < CW; ++t) {
       const int64_t k = k0 + 32 * t + lane;
-      w[t] = k < e ? s.ccol[k] : -1;
+      w[t] = k < e ? BATCH_STREAM_LD(&s.ccol[k]) : -1;
     }
 #pragma unroll
     for (int t = 0; t < CW; ++t) vis[t] = w[t] >= 0 ? s.visit[w[t]] : ~0ull;
@@ -454,7 +467,7 @@ __device__ __noinline__ bool emit_lanes(SlotDev* slots, SlotCtl* sctl, int nslot
   return true;
 }
 
-__global__ void __launch_bounds__(BT)
+__global__ void __launch_bounds__(BT, 4)
     batch_run(SlotDev* slots, SlotCtl* sctl, int nslots, BatchCtl* bc, const ResolveSeg* segs, int maxh) {
   __shared__ int s_cur[MAX_SLOTS_SMEM], s_dir[MAX_SLOTS_SMEM], s_done[MAX_SLOTS_SMEM], s_it[MAX_SLOTS_SMEM];
   __shared__ int64_t s_ncur[MAX_SLOTS_SMEM];
@@ -501,18 +514,30 @@ __global__ void __launch_bounds__(BT)
         // a lane each; long ones: chunks, a warp each, parents by atomicMin.
         // Young lanes (joined one or two boundaries ago) are pushed top-down below; while
         // there are any, next-frontier words are set by atomicOr from both sides.
+        // Without a mailbox, a vertex whose adjacency one thread or one warp scans whole is
+        // committed here (levels, visit word, its degree into m_next): no other reader of
+        // its visit word runs in this phase, and the commit phase skips it.
         const uint64_t yg = early ? *(volatile const uint64_t*)&s.young : 0ull;
         const uint64_t act = *(volatile const uint64_t*)&s.active & ~yg;  // lanes may have joined at the last boundary
+        const uint16_t it1 = (uint16_t)(s_it[si] + 1);
+        int64_t msum = 0;
         for (int64_t i0 = gw * 32; i0 < s.n_lanes; i0 += nw * 32) {
           const int64_t i = i0 + lane;
           int32_t w = -1;
           uint64_t got = 0;
           if (i < s.n_lanes) {
-            w = s.lanes[i];
-            const uint64_t miss = act & ~s.visit[w];
+            w = BATCH_STREAM_LD(&s.lanes[i]);
+            const uint64_t vw = BATCH_STREAM_LD(&s.visit[w]);
+            const uint64_t miss = act & ~vw;
             if (miss) {
-              got = hits_thread(s, fc, w, miss, 0ull, s.crow[w], s.crow[w + 1], w_pull);
+              const int64_t rb = s.crow[w], re = s.crow[w + 1];
+              got = hits_thread(s, fc, w, miss, 0ull, rb, re, w_pull);
               ++v_pull;
+              if (got && !early && FUSE_COMMIT) {
+                set_lane_levels(s, w, got, it1);
+                s.visit[w] = vw | got;
+                msum += re - rb;
+              }
             }
           }
           bool first = got != 0;
@@ -525,9 +550,10 @@ __global__ void __launch_bounds__(BT)
           list_append(first, w, &sctl[si].fl_n[nxt], s.fl[nxt]);
         }
         for (int64_t it = gw; it < s.n_items; it += nw) {
-          const uint64_t item = s.items[it];
+          const uint64_t item = BATCH_STREAM_LD(&s.items[it]);
           const int32_t w = (int32_t)(item >> 32);
-          const uint64_t miss = act & ~s.visit[w];
+          const uint64_t vw = BATCH_STREAM_LD(&s.visit[w]);
+          const uint64_t miss = act & ~vw;
           if (!miss) continue;
           const int64_t rb = s.crow[w], re = s.crow[w + 1];
           const int64_t b = rb + (int64_t)(uint32_t)item * BATCH_CHUNK, e = min(re, b + BATCH_CHUNK);
@@ -535,17 +561,24 @@ __global__ void __launch_bounds__(BT)
           if (lane == 0 && b == rb) ++v_pull;
           const uint64_t got = whole ? hits_warp<false>(s, fc, w, miss, 0ull, b, e, w_pull)
                                      : hits_warp<true>(s, fc, w, miss, 0ull, b, e, w_pull);
+          if (got && whole && !early && FUSE_COMMIT && lane < 8) set_lane_levels_q(s, w, got, it1, lane);
           bool first = false;
           if (got && lane == 0) {
             if (whole && !yg) {
               fn[w] = got;
               first = true;
+              if (!early && FUSE_COMMIT) {
+                s.visit[w] = vw | got;
+                msum += re - rb;
+              }
             } else {
               first = atomicOr((unsigned long long*)&fn[w], (unsigned long long)got) == 0ull;
             }
           }
           list_append(first, w, &sctl[si].fl_n[nxt], s.fl[nxt]);
         }
+        msum = warp_sum(msum);
+        if (lane == 0 && msum) atomicAdd((unsigned long long*)&sctl[si].m_next, (unsigned long long)msum);
         if (yg) {
           // push of the young lanes: frontier entries carrying their bits, found 32 at a time
           // by a ballot; a long adjacency's first chunk here, the others queued for E2
@@ -614,9 +647,11 @@ __global__ void __launch_bounds__(BT)
         ++v_disc;
         const int32_t w = s.fl[nxt][j];
         const uint64_t nb = fn[w];
+        const uint64_t vw = s.visit[w];
+        if ((vw & nb) == nb) continue;  // committed by the pull that found it
         msum += s.crow[w + 1] - s.crow[w];
         set_lane_levels(s, w, nb, it);
-        s.visit[w] |= nb;
+        s.visit[w] = vw | nb;
         alive |= nb;
       }
       msum = warp_sum(msum);
