@@ -11,7 +11,8 @@
 //               chunks, the first pushed by the vertex's warp, the rest queued. Bottom-up
 //               slots pull: every vertex still missing some lanes scans its ascending
 //               adjacency, and the first neighbour carrying a lane's frontier bit is that
-//               lane's parent (so min-id); short adjacencies a lane each, long ones in
+//               lane's parent (so min-id); short adjacencies a lane each, medium ones
+//               (on large cores) 32 to a warp as one flattened sequence, long ones in
 //               chunks a warp each, chunk results merged by atomicMin.
 //   E2 queued   every warp takes queued top-down chunks (only when some slot queued any).
 //   P  commit   every reached lane gets its level; visit |= new lanes (vertices a pull
@@ -70,8 +71,9 @@ struct SlotDev {
   const int32_t* up;
   const int32_t* old2core;
   const int32_t* lanes;   // bottom-up work: short adjacencies, a lane each
+  const int32_t* mids;    // bottom-up work: medium adjacencies, 32 to a warp (hits_lanes32)
   const uint64_t* items;  // bottom-up work: (vertex << 32 | chunk) for long ones, a warp each
-  int64_t n_lanes, n_items;
+  int64_t n_lanes, n_mids, n_items;
   // state (core ids)
   uint64_t* visit;
   uint64_t* front[2];
@@ -219,6 +221,90 @@ __device__ __forceinline__ uint64_t hits_thread(const SlotDev& s, const uint64_t
     }
   }
   ne += min(k, e) - b;
+  return got;
+}
+
+// 32-entry windows per step of the flattened scan (4 windows spill registers of batch_run:
+// 16.16 vs 16.01 ms for 64 roots at scale 24)
+constexpr int CWM = 2;
+
+// The medium adjacencies of a warp's 32 list entries (lane i: vertex w with `want` lanes
+// missing, d entries from rb; d = 0 for none) scanned as one flattened sequence, 32 * CWM
+// entries per step, so that the warp's time follows the entries' total rather than its
+// longest row. Each entry's vertex (its owner lane) is found by a binary search over the
+// lanes' start offsets; a segmented inclusive OR-scan over the lanes, restarted where the
+// owner changes, gives each entry the lanes that an earlier entry of the same vertex already
+// carries, and s_got (this warp's 32 words of shared memory) holds per vertex the lanes
+// found in earlier windows. So every lane of `want` takes the first entry carrying it (the
+// smallest neighbour id), as in the ascending scan of hits_thread. Returns, in lane i, the
+// lanes found for lane i's vertex. All 32 threads of the warp must call.
+__device__ __forceinline__ uint64_t hits_lanes32(const SlotDev& s, const uint64_t* __restrict__ fc, int32_t w,
+                                                 uint64_t want, int64_t rb, int32_t d, uint64_t* s_got,
+                                                 int64_t& ne) {
+  const int lane = threadIdx.x & 31;
+  const int32_t incl = warp_incl_scan(d);
+  const int32_t total = __shfl_sync(FULL, incl, 31);
+  const int32_t start = incl - d;
+  s_got[lane] = 0ull;
+  uint64_t got = 0;
+  __syncwarp();
+  for (int32_t r0 = 0; r0 < total; r0 += 32 * CWM) {
+    if (__all_sync(FULL, got == want)) break;  // every vertex has all its lanes
+    const uint64_t open = want & ~got;
+    int32_t u[CWM], own[CWM];
+    uint64_t h[CWM];
+#pragma unroll
+    for (int t = 0; t < CWM; ++t) {
+      const int32_t idx = r0 + 32 * t + lane;
+      int o = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int cand = o + step;
+        if (__shfl_sync(FULL, start, cand) <= idx) o = cand;
+      }
+      own[t] = o;
+      const int64_t orb = __shfl_sync(FULL, rb, o);
+      const int32_t ost = __shfl_sync(FULL, start, o);
+      const uint64_t oopen = __shfl_sync(FULL, open, o);
+      u[t] = idx < total && oopen ? BATCH_STREAM_LD(&s.ccol[orb + (idx - ost)]) : -1;
+      h[t] = oopen;
+    }
+#pragma unroll
+    for (int t = 0; t < CWM; ++t) {
+      if (u[t] >= 0) ++ne;
+      h[t] = u[t] >= 0 ? fc[u[t]] & h[t] : 0ull;
+    }
+#pragma unroll
+    for (int t = 0; t < CWM; ++t) {
+      if (!__any_sync(FULL, h[t] != 0)) continue;
+      uint64_t inc = h[t];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(FULL, inc, o);
+        const int yo = __shfl_up_sync(FULL, own[t], o);
+        if (lane >= o && yo == own[t]) inc |= y;
+      }
+      const uint64_t ex = __shfl_up_sync(FULL, inc, 1);
+      const int po = __shfl_up_sync(FULL, own[t], 1);
+      const int no = __shfl_down_sync(FULL, own[t], 1);
+      const int32_t ow = __shfl_sync(FULL, w, own[t]);
+      const uint64_t prev = s_got[own[t]];
+      uint64_t mine = h[t] & ~prev & ~((lane > 0 && po == own[t]) ? ex : 0ull);
+      if (mine) {
+        int32_t* prow = s.P + (int64_t)ow * 64;
+        const int32_t uo = s.new2old[u[t]];
+        while (mine) {
+          const int l = __ffsll((long long)mine) - 1;
+          mine &= mine - 1;
+          prow[l] = uo;
+        }
+      }
+      __syncwarp();
+      if ((lane == 31 || no != own[t]) && inc) s_got[own[t]] = prev | inc;  // segment end
+      __syncwarp();
+    }
+    got = s_got[lane];
+  }
   return got;
 }
 
@@ -471,6 +557,7 @@ __global__ void __launch_bounds__(BT, 4)
     batch_run(SlotDev* slots, SlotCtl* sctl, int nslots, BatchCtl* bc, const ResolveSeg* segs, int maxh) {
   __shared__ int s_cur[MAX_SLOTS_SMEM], s_dir[MAX_SLOTS_SMEM], s_done[MAX_SLOTS_SMEM], s_it[MAX_SLOTS_SMEM];
   __shared__ int64_t s_ncur[MAX_SLOTS_SMEM];
+  __shared__ uint64_t s_got[BT / 32][32];  // per warp: lanes found per vertex (hits_lanes32)
   const bool early = slots[0].mb != nullptr;
   const int lane = threadIdx.x & 31;
   const int64_t gw = gtid() >> 5, nw = gthreads() >> 5;
@@ -511,7 +598,8 @@ __global__ void __launch_bounds__(BT, 4)
       } else {
         // pull: every core vertex still missing lanes scans its ascending adjacency for the
         // first neighbour carrying each missing lane (min-id parents). Short adjacencies:
-        // a lane each; long ones: chunks, a warp each, parents by atomicMin.
+        // a lane each; medium ones (large cores): 32 to a warp, flattened; long ones:
+        // chunks, a warp each, parents by atomicMin.
         // Young lanes (joined one or two boundaries ago) are pushed top-down below; while
         // there are any, next-frontier words are set by atomicOr from both sides.
         // Without a mailbox, a vertex whose adjacency one thread or one warp scans whole is
@@ -539,6 +627,36 @@ __global__ void __launch_bounds__(BT, 4)
                 msum += re - rb;
               }
             }
+          }
+          bool first = got != 0;
+          if (got) {
+            if (yg)
+              first = atomicOr((unsigned long long*)&fn[w], (unsigned long long)got) == 0ull;
+            else
+              fn[w] = got;
+          }
+          list_append(first, w, &sctl[si].fl_n[nxt], s.fl[nxt]);
+        }
+        for (int64_t i0 = gw * 32; i0 < s.n_mids; i0 += nw * 32) {
+          const int64_t i = i0 + lane;
+          int32_t w = -1, d = 0;
+          int64_t rb = 0;
+          uint64_t miss = 0, vw = 0, got = 0;
+          if (i < s.n_mids) {
+            w = BATCH_STREAM_LD(&s.mids[i]);
+            vw = BATCH_STREAM_LD(&s.visit[w]);
+            miss = act & ~vw;
+            if (miss) {
+              rb = s.crow[w];
+              d = (int32_t)(s.crow[w + 1] - rb);
+              ++v_pull;
+            }
+          }
+          if (__any_sync(FULL, d > 0)) got = hits_lanes32(s, fc, w, miss, rb, d, s_got[threadIdx.x >> 5], w_pull);
+          if (got && !early && FUSE_COMMIT) {
+            set_lane_levels(s, w, got, it1);
+            s.visit[w] = vw | got;
+            msum += d;
           }
           bool first = got != 0;
           if (got) {
@@ -1043,8 +1161,10 @@ int batch_launch(BatchCtx* ctx, const SlotSpec* specs, int nspecs, int sm_share,
     d.up = g->up;
     d.old2core = g->old2core;
     d.lanes = g->batch_lane;
+    d.mids = g->batch_mid;
     d.items = g->batch_item;
     d.n_lanes = g->n_batch_lane;
+    d.n_mids = g->n_batch_mid;
     d.n_items = g->n_batch_item;
     d.visit = (uint64_t*)sp.mem[0];
     d.front[0] = (uint64_t*)sp.mem[1];

@@ -272,21 +272,26 @@ __global__ void list_anchors(int64_t nc, const uint8_t* __restrict__ aflag, cons
   }
 }
 
-// Work lists of the batched traversal: short adjacencies one per lane, long ones in chunks.
-__global__ void batch_work_count(int64_t nc, const int64_t* __restrict__ crow, uint8_t* __restrict__ short_flag,
+// Work lists of the batched traversal: short adjacencies one per lane, medium ones (large
+// cores only: mid_max > BATCH_LANE_DEG) 32 to a warp, long ones in chunks.
+__global__ void batch_work_count(int64_t nc, const int64_t* __restrict__ crow, int mid_max,
+                                 uint8_t* __restrict__ short_flag, uint8_t* __restrict__ mid_flag,
                                  int32_t* __restrict__ nchunks) {
   for (int64_t v = gtid(); v < nc; v += gthreads()) {
     const int64_t d = crow[v + 1] - crow[v];
     short_flag[v] = d > 0 && d <= BATCH_LANE_DEG;
-    nchunks[v] = d > BATCH_LANE_DEG ? (int32_t)((d + BATCH_CHUNK - 1) / BATCH_CHUNK) : 0;
+    mid_flag[v] = d > BATCH_LANE_DEG && d <= mid_max;
+    nchunks[v] = d > mid_max ? (int32_t)((d + BATCH_CHUNK - 1) / BATCH_CHUNK) : 0;
   }
 }
 
 __global__ void batch_work_fill(int64_t nc, const uint8_t* __restrict__ short_flag, const int32_t* __restrict__ lpos,
+                                const uint8_t* __restrict__ mid_flag, const int32_t* __restrict__ mpos,
                                 const int32_t* __restrict__ nchunks, const int64_t* __restrict__ ipos,
-                                int32_t* __restrict__ lanes, uint64_t* __restrict__ items) {
+                                int32_t* __restrict__ lanes, int32_t* __restrict__ mids, uint64_t* __restrict__ items) {
   for (int64_t v = gtid(); v < nc; v += gthreads()) {
     if (short_flag[v]) lanes[lpos[v]] = (int32_t)v;
+    if (mid_flag[v]) mids[mpos[v]] = (int32_t)v;
     for (int32_t c = 0; c < nchunks[v]; ++c) items[ipos[v] + c] = ((uint64_t)v << 32) | (uint32_t)c;
   }
 }
@@ -492,6 +497,7 @@ void free_graph(gt_graph* g) {
   cudaFree(g->anchor_vid);
   cudaFree(g->anchor_out);
   cudaFree(g->batch_lane);
+  cudaFree(g->batch_mid);
   cudaFree(g->batch_item);
   cudaFree(g->new2old);
   cudaFree(g->old2core);
@@ -697,28 +703,38 @@ int build_graph(gt_graph* g, const int64_t* edges, int64_t m, int64_t n, cudaStr
 
   // ---- batched traversal work lists
   {
-    uint8_t* sflag;
-    int32_t *lpos, *nch;
+    uint8_t *sflag, *mflag;
+    int32_t *lpos, *mpos, *nch;
     int64_t* ipos;
     const int64_t nc1 = std::max<int64_t>(nc, 1);
     TRY(tmp_malloc(tmp, (void**)&sflag, nc1));
+    TRY(tmp_malloc(tmp, (void**)&mflag, nc1));
     TRY(tmp_malloc(tmp, (void**)&lpos, sizeof(int32_t) * (nc + 1)));
+    TRY(tmp_malloc(tmp, (void**)&mpos, sizeof(int32_t) * (nc + 1)));
     TRY(tmp_malloc(tmp, (void**)&nch, sizeof(int32_t) * nc1));
     TRY(tmp_malloc(tmp, (void**)&ipos, sizeof(int64_t) * (nc + 1)));
-    if (nc > 0) batch_work_count<<<grid_for(g, nc), BT, 0, s>>>(nc, cv.row, sflag, nch);
+    // medium list on large cores only: on small ones the flattened scan's serial steps
+    // cost more than one warp per vertex (measured at R-MAT scales 16-24)
+    const int mid_max = nc >= BATCH_MID_MIN_CORE ? BATCH_MID_DEG : BATCH_LANE_DEG;
+    if (nc > 0) batch_work_count<<<grid_for(g, nc), BT, 0, s>>>(nc, cv.row, mid_max, sflag, mflag, nch);
     TRY(scan_u8_to_i32(sflag, lpos, nc, s, d_scan, scan_bytes));
+    TRY(scan_u8_to_i32(mflag, mpos, nc, s, d_scan, scan_bytes));
     TRY(scan_i32_to_i64(nch, ipos, nc, s, d_scan, scan_bytes));
-    int32_t nl = 0;
+    int32_t nl = 0, nm = 0;
     int64_t ni = 0;
     TRYC(cudaMemcpyAsync(&nl, lpos + nc, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "readback");
+    TRYC(cudaMemcpyAsync(&nm, mpos + nc, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "readback");
     TRYC(cudaMemcpyAsync(&ni, ipos + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s), "readback");
     TRYC(cudaStreamSynchronize(s), "sync");
     g->n_batch_lane = nl;
+    g->n_batch_mid = nm;
     g->n_batch_item = ni;
     TRY(device_malloc(g, (void**)&g->batch_lane, sizeof(int32_t) * std::max<int64_t>(nl, 1)));
+    TRY(device_malloc(g, (void**)&g->batch_mid, sizeof(int32_t) * std::max<int64_t>(nm, 1)));
     TRY(device_malloc(g, (void**)&g->batch_item, sizeof(uint64_t) * std::max<int64_t>(ni, 1)));
     if (nc > 0)
-      batch_work_fill<<<grid_for(g, nc), BT, 0, s>>>(nc, sflag, lpos, nch, ipos, g->batch_lane, g->batch_item);
+      batch_work_fill<<<grid_for(g, nc), BT, 0, s>>>(nc, sflag, lpos, mflag, mpos, nch, ipos, g->batch_lane,
+                                                     g->batch_mid, g->batch_item);
     TRYC(cudaGetLastError(), "batch work lists");
   }
 

@@ -22,9 +22,12 @@ constexpr int BU_CHUNK_WORDS = 128;     // bitmap words one warp takes per step 
 // (bin 1), a CTA (bin 2) or the whole grid (bin 3).
 constexpr int NBINS = 4;
 // Batched traversal work split: core vertices of degree <= BATCH_LANE_DEG are scanned by
-// one lane each; longer adjacencies are cut into chunks of BATCH_CHUNK entries, each a
-// work item for a warp.
+// one lane each; on graphs with at least BATCH_MID_MIN_CORE core vertices, those of degree
+// up to BATCH_MID_DEG are scanned 32 to a warp as one flattened sequence; longer
+// adjacencies are cut into chunks of BATCH_CHUNK entries, each a work item for a warp.
 constexpr int BATCH_LANE_DEG = 32;
+constexpr int BATCH_MID_DEG = 128;
+constexpr int64_t BATCH_MID_MIN_CORE = 1 << 19;
 constexpr int BATCH_CHUNK = 2048;
 
 // Per-traversal control block in device memory. Kernels read the direction and buffer
@@ -125,6 +128,8 @@ struct gt_graph {
   // batched traversal work lists over the core (built with the graph)
   int64_t n_batch_lane = 0;
   int32_t* batch_lane = nullptr;    // core vertices of degree 1..BATCH_LANE_DEG
+  int64_t n_batch_mid = 0;
+  int32_t* batch_mid = nullptr;     // core vertices of degree BATCH_LANE_DEG+1..BATCH_MID_DEG (large cores)
   int64_t n_batch_item = 0;
   uint64_t* batch_item = nullptr;   // (core id << 32) | chunk index, for longer adjacencies
   int32_t* new2old = nullptr;   // core id -> vertex id

@@ -17,14 +17,14 @@ namespace gt {
 namespace {
 
 constexpr char MAGIC[8] = {'G', 'T', 'G', 'R', 'A', 'P', 'H', '1'};
-constexpr uint32_t VERSION = 1;
+constexpr uint32_t VERSION = 2;
 constexpr size_t PIECE = size_t(64) << 20;
 
 struct FileHeader {
   char magic[8];
   uint32_t version;
   uint32_t header_bytes;
-  int64_t n, m, nnz, n_core, nnz_core, n_anchor, n_batch_lane, n_batch_item, resolve_n;
+  int64_t n, m, nnz, n_core, nnz_core, n_anchor, n_batch_lane, n_batch_mid, n_batch_item, resolve_n;
   int32_t resolve_heights, pad;
   gt_config cfg;
   gt_tuning tuning;
@@ -90,6 +90,7 @@ int save_graph(const gt_graph* g, FILE* f, cudaStream_t s) {
   h.nnz_core = g->core.nnz;
   h.n_anchor = g->n_anchor;
   h.n_batch_lane = g->n_batch_lane;
+  h.n_batch_mid = g->n_batch_mid;
   h.n_batch_item = g->n_batch_item;
   h.resolve_n = g->resolve_n;
   h.resolve_heights = g->resolve_heights;
@@ -117,6 +118,7 @@ int save_graph(const gt_graph* g, FILE* f, cudaStream_t s) {
       {g->anchor_cid, sizeof(int32_t) * g->n_anchor},
       {g->anchor_vid, sizeof(int32_t) * g->n_anchor},
       {g->batch_lane, sizeof(int32_t) * g->n_batch_lane},
+      {g->batch_mid, sizeof(int32_t) * g->n_batch_mid},
       {g->batch_item, sizeof(uint64_t) * g->n_batch_item},
       {g->resolve_list, sizeof(int32_t) * g->resolve_n},
       {g->resolve_up, sizeof(int32_t) * g->resolve_n},
@@ -139,7 +141,7 @@ int load_graph(gt_graph* g, FILE* f, cudaStream_t s) {
     return io_error("gt_graph_load: not a graph saved by this version of gt_graph_save");
   if (h.n < 1 || h.n > 0x7FFFFFFFLL || h.nnz < 0 || h.n_core < 0 || h.n_core > h.n || h.nnz_core < 0 ||
       h.nnz_core > h.nnz || h.n_anchor < 0 || h.n_anchor > h.n_core || h.resolve_n < 0 || h.resolve_n > h.n ||
-      h.resolve_heights < 0 || h.resolve_heights > 1 << 20 || h.n_batch_lane < 0 || h.n_batch_item < 0)
+      h.resolve_heights < 0 || h.resolve_heights > 1 << 20 || h.n_batch_lane < 0 || h.n_batch_mid < 0 || h.n_batch_item < 0)
     return io_error("gt_graph_load: the header's sizes are inconsistent");
   g->n = h.n;
   g->m = h.m;
@@ -148,6 +150,7 @@ int load_graph(gt_graph* g, FILE* f, cudaStream_t s) {
   g->tuning = h.tuning;
   g->n_anchor = h.n_anchor;
   g->n_batch_lane = h.n_batch_lane;
+  g->n_batch_mid = h.n_batch_mid;
   g->n_batch_item = h.n_batch_item;
   g->resolve_n = h.resolve_n;
   const int64_t n = h.n, nc = h.n_core;
@@ -173,6 +176,7 @@ int load_graph(gt_graph* g, FILE* f, cudaStream_t s) {
       {(void**)&g->anchor_cid, sizeof(int32_t) * h.n_anchor, 0},
       {(void**)&g->anchor_vid, sizeof(int32_t) * h.n_anchor, 0},
       {(void**)&g->batch_lane, sizeof(int32_t) * h.n_batch_lane, 0},
+      {(void**)&g->batch_mid, sizeof(int32_t) * h.n_batch_mid, 0},
       {(void**)&g->batch_item, sizeof(uint64_t) * h.n_batch_item, 0},
       {(void**)&g->resolve_list, sizeof(int32_t) * h.resolve_n, 0},
       {(void**)&g->resolve_up, sizeof(int32_t) * h.resolve_n, 0},

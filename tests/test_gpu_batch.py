@@ -209,3 +209,24 @@ def test_batch_work_counts(torch):
     w = gt.gt_bfs_batch_work(g)
     assert w["pull_entries"] > 0 and w["push_entries"] > 0 and w["pull_vertices"] > 0
     assert w["discovered"] >= int(core.sum() * 0.5)
+
+
+def test_batch_large_core_medium_rows(torch):
+    """R-MAT scale 21: its core (about 966 K vertices) is above the size (2^19) from which
+    core vertices of degree 33-128 are scanned 32 to a warp as one flattened sequence, so
+    all three work lists (short rows a lane each, medium rows flattened, long rows in
+    chunks) take part; every row must equal the oracle."""
+    scale = 21
+    n = 1 << scale
+    e = graphgen.rmat_edges(scale, 16, seed=41)
+    og = OracleGraph(e, n)
+    g = gt.gt_graph_build(e, n)
+    assert g.stats()["n_core"] >= 1 << 19
+    row, col = og.csr()
+    vt = g.vertex_type()
+    core = np.isin(vt, [0, 1])
+    cdeg = np.bincount(np.repeat(np.arange(n), np.diff(row))[core[col]], minlength=n)[core]
+    assert ((cdeg > 32) & (cdeg <= 128)).sum() > 1000  # medium rows present
+    roots = graphgen.pick_roots(42, n, 64, og.degree()).tolist()
+    (P,), (L,) = run_batch(torch, [g], [roots])
+    check_rows(P, L, og, roots, "s21 large core")
