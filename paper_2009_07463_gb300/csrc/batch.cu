@@ -72,7 +72,7 @@ struct SlotDev {
   const int32_t* old2core;
   const int32_t* lanes;   // bottom-up work: short adjacencies, a lane each
   const int32_t* mids;    // bottom-up work: medium adjacencies, 32 to a warp (hits_lanes32)
-  const uint64_t* items;  // bottom-up work: (vertex << 32 | chunk) for long ones, a warp each
+  const BatchItem* items; // bottom-up work: chunks of the long ones, a warp each
   int64_t n_lanes, n_mids, n_items;
   // state (core ids)
   uint64_t* visit;
@@ -668,15 +668,16 @@ __global__ void __launch_bounds__(BT, 4)
           list_append(first, w, &sctl[si].fl_n[nxt], s.fl[nxt]);
         }
         for (int64_t it = gw; it < s.n_items; it += nw) {
-          const uint64_t item = BATCH_STREAM_LD(&s.items[it]);
-          const int32_t w = (int32_t)(item >> 32);
+          const int4 rec = BATCH_STREAM_LD(reinterpret_cast<const int4*>(s.items) + it);
+          const int64_t b = (int64_t)(((uint64_t)(uint32_t)rec.y << 32) | (uint32_t)rec.x);
+          const int32_t w = rec.z;
+          const uint32_t meta = (uint32_t)rec.w;
+          const int64_t e = b + (meta & BATCH_ITEM_LEN);
           const uint64_t vw = BATCH_STREAM_LD(&s.visit[w]);
           const uint64_t miss = act & ~vw;
           if (!miss) continue;
-          const int64_t rb = s.crow[w], re = s.crow[w + 1];
-          const int64_t b = rb + (int64_t)(uint32_t)item * BATCH_CHUNK, e = min(re, b + BATCH_CHUNK);
-          const bool whole = b == rb && e == re;
-          if (lane == 0 && b == rb) ++v_pull;
+          const bool whole = meta & BATCH_ITEM_WHOLE;
+          if (lane == 0 && (meta & BATCH_ITEM_FIRST)) ++v_pull;
           const uint64_t got = whole ? hits_warp<false>(s, fc, w, miss, 0ull, b, e, w_pull)
                                      : hits_warp<true>(s, fc, w, miss, 0ull, b, e, w_pull);
           if (got && whole && !early && FUSE_COMMIT && lane < 8) set_lane_levels_q(s, w, got, it1, lane);
@@ -687,7 +688,7 @@ __global__ void __launch_bounds__(BT, 4)
               first = true;
               if (!early && FUSE_COMMIT) {
                 s.visit[w] = vw | got;
-                msum += re - rb;
+                msum += e - b;
               }
             } else {
               first = atomicOr((unsigned long long*)&fn[w], (unsigned long long)got) == 0ull;

@@ -285,14 +285,24 @@ __global__ void batch_work_count(int64_t nc, const int64_t* __restrict__ crow, i
   }
 }
 
-__global__ void batch_work_fill(int64_t nc, const uint8_t* __restrict__ short_flag, const int32_t* __restrict__ lpos,
-                                const uint8_t* __restrict__ mid_flag, const int32_t* __restrict__ mpos,
-                                const int32_t* __restrict__ nchunks, const int64_t* __restrict__ ipos,
-                                int32_t* __restrict__ lanes, int32_t* __restrict__ mids, uint64_t* __restrict__ items) {
+__global__ void batch_work_fill(int64_t nc, const int64_t* __restrict__ crow, const uint8_t* __restrict__ short_flag,
+                                const int32_t* __restrict__ lpos, const uint8_t* __restrict__ mid_flag,
+                                const int32_t* __restrict__ mpos, const int32_t* __restrict__ nchunks,
+                                const int64_t* __restrict__ ipos, int32_t* __restrict__ lanes,
+                                int32_t* __restrict__ mids, BatchItem* __restrict__ items) {
   for (int64_t v = gtid(); v < nc; v += gthreads()) {
     if (short_flag[v]) lanes[lpos[v]] = (int32_t)v;
     if (mid_flag[v]) mids[mpos[v]] = (int32_t)v;
-    for (int32_t c = 0; c < nchunks[v]; ++c) items[ipos[v] + c] = ((uint64_t)v << 32) | (uint32_t)c;
+    const int32_t nch = nchunks[v];
+    const int64_t rb = crow[v], re = crow[v + 1];
+    for (int32_t c = 0; c < nch; ++c) {
+      BatchItem it;
+      it.b = rb + (int64_t)c * BATCH_CHUNK;
+      it.w = (int32_t)v;
+      it.meta = (uint32_t)min((int64_t)BATCH_CHUNK, re - it.b) | (c == 0 ? BATCH_ITEM_FIRST : 0u) |
+                (nch == 1 ? BATCH_ITEM_WHOLE : 0u);
+      items[ipos[v] + c] = it;
+    }
   }
 }
 
@@ -731,10 +741,10 @@ int build_graph(gt_graph* g, const int64_t* edges, int64_t m, int64_t n, cudaStr
     g->n_batch_item = ni;
     TRY(device_malloc(g, (void**)&g->batch_lane, sizeof(int32_t) * std::max<int64_t>(nl, 1)));
     TRY(device_malloc(g, (void**)&g->batch_mid, sizeof(int32_t) * std::max<int64_t>(nm, 1)));
-    TRY(device_malloc(g, (void**)&g->batch_item, sizeof(uint64_t) * std::max<int64_t>(ni, 1)));
+    TRY(device_malloc(g, (void**)&g->batch_item, sizeof(BatchItem) * std::max<int64_t>(ni, 1)));
     if (nc > 0)
-      batch_work_fill<<<grid_for(g, nc), BT, 0, s>>>(nc, sflag, lpos, mflag, mpos, nch, ipos, g->batch_lane,
-                                                     g->batch_mid, g->batch_item);
+      batch_work_fill<<<grid_for(g, nc), BT, 0, s>>>(nc, cv.row, sflag, lpos, mflag, mpos, nch, ipos,
+                                                     g->batch_lane, g->batch_mid, g->batch_item);
     TRYC(cudaGetLastError(), "batch work lists");
   }
 

@@ -29,6 +29,18 @@ constexpr int BATCH_LANE_DEG = 32;
 constexpr int BATCH_MID_DEG = 128;
 constexpr int64_t BATCH_MID_MIN_CORE = 1 << 19;
 constexpr int BATCH_CHUNK = 2048;
+// A long-row work item: entries [b, b + (meta & BATCH_ITEM_LEN)) of core vertex w's
+// adjacency (a chunk of at most BATCH_CHUNK entries); meta also flags a chunk that is the
+// whole row and a chunk that is the row's first.
+struct BatchItem {
+  int64_t b;
+  int32_t w;
+  uint32_t meta;
+};
+static_assert(sizeof(BatchItem) == 16, "one 16-byte load per item");
+constexpr uint32_t BATCH_ITEM_LEN = 0xFFFFu;
+constexpr uint32_t BATCH_ITEM_FIRST = 1u << 30;
+constexpr uint32_t BATCH_ITEM_WHOLE = 1u << 31;
 
 // Per-traversal control block in device memory. Kernels read the direction and buffer
 // selectors from here, so the level loop can run without the host (CUDA graph with a
@@ -131,7 +143,7 @@ struct gt_graph {
   int64_t n_batch_mid = 0;
   int32_t* batch_mid = nullptr;     // core vertices of degree BATCH_LANE_DEG+1..BATCH_MID_DEG (large cores)
   int64_t n_batch_item = 0;
-  uint64_t* batch_item = nullptr;   // (core id << 32) | chunk index, for longer adjacencies
+  gt::BatchItem* batch_item = nullptr;  // chunks of the longer adjacencies
   int32_t* new2old = nullptr;   // core id -> vertex id
   int32_t* old2core = nullptr;  // vertex id -> core id or -1
   int32_t* resolve_list = nullptr;  // tree vertices whose up is a tree vertex, by height desc

@@ -119,7 +119,7 @@ int save_graph(const gt_graph* g, FILE* f, cudaStream_t s) {
       {g->anchor_vid, sizeof(int32_t) * g->n_anchor},
       {g->batch_lane, sizeof(int32_t) * g->n_batch_lane},
       {g->batch_mid, sizeof(int32_t) * g->n_batch_mid},
-      {g->batch_item, sizeof(uint64_t) * g->n_batch_item},
+      {g->batch_item, sizeof(BatchItem) * g->n_batch_item},
       {g->resolve_list, sizeof(int32_t) * g->resolve_n},
       {g->resolve_up, sizeof(int32_t) * g->resolve_n},
   };
@@ -177,7 +177,7 @@ int load_graph(gt_graph* g, FILE* f, cudaStream_t s) {
       {(void**)&g->anchor_vid, sizeof(int32_t) * h.n_anchor, 0},
       {(void**)&g->batch_lane, sizeof(int32_t) * h.n_batch_lane, 0},
       {(void**)&g->batch_mid, sizeof(int32_t) * h.n_batch_mid, 0},
-      {(void**)&g->batch_item, sizeof(uint64_t) * h.n_batch_item, 0},
+      {(void**)&g->batch_item, sizeof(BatchItem) * h.n_batch_item, 0},
       {(void**)&g->resolve_list, sizeof(int32_t) * h.resolve_n, 0},
       {(void**)&g->resolve_up, sizeof(int32_t) * h.resolve_n, 0},
   };
