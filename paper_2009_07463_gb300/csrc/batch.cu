@@ -107,7 +107,29 @@ struct SlotCtl {
   int32_t cur, dir, done, iter;
   uint64_t alive;  // lanes present in the next frontier (early completion)
   uint64_t fin;    // lanes whose results are written at this level boundary
+  // pull work handed out during a level (long items, medium groups, short groups of 32)
+  unsigned grab[3];
 };
+
+// Pull work is handed out dynamically: a warp takes a few tasks (items, or groups of 32
+// list entries) per atomic on its slot's counter, so that no warp idles at the phase's grid
+// barrier while others still hold work (with a fixed round-robin share, the last warp of a
+// scale-24 pull level finished 1.0-1.4 ms after the first). A take is about 1/GRAB_ROUNDS
+// of a warp's fair share, between 1 and GRAB_MAX tasks.
+#ifndef GRAB_ROUNDS
+#define GRAB_ROUNDS 8
+#endif
+constexpr int GRAB_MAX = 16;
+__device__ __forceinline__ int grab_size(int ntask, int64_t nwarps) {
+  return (int)max((int64_t)1, min((int64_t)GRAB_MAX, (int64_t)ntask / (nwarps * GRAB_ROUNDS)));
+}
+
+// Issues the atomic that reserves this warp's next n tasks; lane 0 holds the result. Task
+// counts of a list fit in 32 bits (items: at most nnz / BATCH_CHUNK + core vertices).
+__device__ __forceinline__ unsigned grab_issue(unsigned* cnt, int n) {
+  return (threadIdx.x & 31) == 0 ? atomicAdd(cnt, (unsigned)n) : 0u;
+}
+__device__ __forceinline__ int grab_take(unsigned issued) { return (int)__shfl_sync(FULL, issued, 0); }
 
 struct ResolveSeg {
   const int32_t* list;
@@ -609,92 +631,126 @@ __global__ void __launch_bounds__(BT, 4)
         const uint64_t act = *(volatile const uint64_t*)&s.active & ~yg;  // lanes may have joined at the last boundary
         const uint16_t it1 = (uint16_t)(s_it[si] + 1);
         int64_t msum = 0;
-        for (int64_t i0 = gw * 32; i0 < s.n_lanes; i0 += nw * 32) {
-          const int64_t i = i0 + lane;
-          int32_t w = -1;
-          uint64_t got = 0;
-          if (i < s.n_lanes) {
-            w = BATCH_STREAM_LD(&s.lanes[i]);
-            const uint64_t vw = BATCH_STREAM_LD(&s.visit[w]);
-            const uint64_t miss = act & ~vw;
-            if (miss) {
-              const int64_t rb = s.crow[w], re = s.crow[w + 1];
-              got = hits_thread(s, fc, w, miss, 0ull, rb, re, w_pull);
-              ++v_pull;
+        // long rows first, then medium, then short ones: the small tasks fill the tail
+        {
+          const int ntask = (int)s.n_items;
+          unsigned* cnt = &sctl[si].grab[0];
+          const int gsz = grab_size(ntask, nw);
+          int t0 = grab_take(grab_issue(cnt, gsz));
+          while (t0 < ntask) {
+            const unsigned nx = grab_issue(cnt, gsz);  // next tasks, in flight meanwhile
+            for (int task = t0; task < min(t0 + gsz, ntask); ++task) {
+              const int64_t it = task;
+              const int4 rec = BATCH_STREAM_LD(reinterpret_cast<const int4*>(s.items) + it);
+              const int64_t b = (int64_t)(((uint64_t)(uint32_t)rec.y << 32) | (uint32_t)rec.x);
+              const int32_t w = rec.z;
+              const uint32_t meta = (uint32_t)rec.w;
+              const int64_t e = b + (meta & BATCH_ITEM_LEN);
+              const uint64_t vw = BATCH_STREAM_LD(&s.visit[w]);
+              const uint64_t miss = act & ~vw;
+              if (!miss) continue;
+              const bool whole = meta & BATCH_ITEM_WHOLE;
+              if (lane == 0 && (meta & BATCH_ITEM_FIRST)) ++v_pull;
+              const uint64_t got = whole ? hits_warp<false>(s, fc, w, miss, 0ull, b, e, w_pull)
+                                         : hits_warp<true>(s, fc, w, miss, 0ull, b, e, w_pull);
+              if (got && whole && !early && FUSE_COMMIT && lane < 8) set_lane_levels_q(s, w, got, it1, lane);
+              bool first = false;
+              if (got && lane == 0) {
+                if (whole && !yg) {
+                  fn[w] = got;
+                  first = true;
+                  if (!early && FUSE_COMMIT) {
+                    s.visit[w] = vw | got;
+                    msum += e - b;
+                  }
+                } else {
+                  first = atomicOr((unsigned long long*)&fn[w], (unsigned long long)got) == 0ull;
+                }
+              }
+              list_append(first, w, &sctl[si].fl_n[nxt], s.fl[nxt]);
+            }
+            t0 = grab_take(nx);
+          }
+        }
+        {
+          const int ntask = (int)((s.n_mids + 31) / 32);
+          unsigned* cnt = &sctl[si].grab[1];
+          const int gsz = grab_size(ntask, nw);
+          int t0 = grab_take(grab_issue(cnt, gsz));
+          while (t0 < ntask) {
+            const unsigned nx = grab_issue(cnt, gsz);  // next tasks, in flight meanwhile
+            for (int task = t0; task < min(t0 + gsz, ntask); ++task) {
+              const int64_t i0 = (int64_t)task * 32;
+              const int64_t i = i0 + lane;
+              int32_t w = -1, d = 0;
+              int64_t rb = 0;
+              uint64_t miss = 0, vw = 0, got = 0;
+              if (i < s.n_mids) {
+                w = BATCH_STREAM_LD(&s.mids[i]);
+                vw = BATCH_STREAM_LD(&s.visit[w]);
+                miss = act & ~vw;
+                if (miss) {
+                  rb = s.crow[w];
+                  d = (int32_t)(s.crow[w + 1] - rb);
+                  ++v_pull;
+                }
+              }
+              if (__any_sync(FULL, d > 0)) got = hits_lanes32(s, fc, w, miss, rb, d, s_got[threadIdx.x >> 5], w_pull);
               if (got && !early && FUSE_COMMIT) {
                 set_lane_levels(s, w, got, it1);
                 s.visit[w] = vw | got;
-                msum += re - rb;
+                msum += d;
               }
-            }
-          }
-          bool first = got != 0;
-          if (got) {
-            if (yg)
-              first = atomicOr((unsigned long long*)&fn[w], (unsigned long long)got) == 0ull;
-            else
-              fn[w] = got;
-          }
-          list_append(first, w, &sctl[si].fl_n[nxt], s.fl[nxt]);
-        }
-        for (int64_t i0 = gw * 32; i0 < s.n_mids; i0 += nw * 32) {
-          const int64_t i = i0 + lane;
-          int32_t w = -1, d = 0;
-          int64_t rb = 0;
-          uint64_t miss = 0, vw = 0, got = 0;
-          if (i < s.n_mids) {
-            w = BATCH_STREAM_LD(&s.mids[i]);
-            vw = BATCH_STREAM_LD(&s.visit[w]);
-            miss = act & ~vw;
-            if (miss) {
-              rb = s.crow[w];
-              d = (int32_t)(s.crow[w + 1] - rb);
-              ++v_pull;
-            }
-          }
-          if (__any_sync(FULL, d > 0)) got = hits_lanes32(s, fc, w, miss, rb, d, s_got[threadIdx.x >> 5], w_pull);
-          if (got && !early && FUSE_COMMIT) {
-            set_lane_levels(s, w, got, it1);
-            s.visit[w] = vw | got;
-            msum += d;
-          }
-          bool first = got != 0;
-          if (got) {
-            if (yg)
-              first = atomicOr((unsigned long long*)&fn[w], (unsigned long long)got) == 0ull;
-            else
-              fn[w] = got;
-          }
-          list_append(first, w, &sctl[si].fl_n[nxt], s.fl[nxt]);
-        }
-        for (int64_t it = gw; it < s.n_items; it += nw) {
-          const int4 rec = BATCH_STREAM_LD(reinterpret_cast<const int4*>(s.items) + it);
-          const int64_t b = (int64_t)(((uint64_t)(uint32_t)rec.y << 32) | (uint32_t)rec.x);
-          const int32_t w = rec.z;
-          const uint32_t meta = (uint32_t)rec.w;
-          const int64_t e = b + (meta & BATCH_ITEM_LEN);
-          const uint64_t vw = BATCH_STREAM_LD(&s.visit[w]);
-          const uint64_t miss = act & ~vw;
-          if (!miss) continue;
-          const bool whole = meta & BATCH_ITEM_WHOLE;
-          if (lane == 0 && (meta & BATCH_ITEM_FIRST)) ++v_pull;
-          const uint64_t got = whole ? hits_warp<false>(s, fc, w, miss, 0ull, b, e, w_pull)
-                                     : hits_warp<true>(s, fc, w, miss, 0ull, b, e, w_pull);
-          if (got && whole && !early && FUSE_COMMIT && lane < 8) set_lane_levels_q(s, w, got, it1, lane);
-          bool first = false;
-          if (got && lane == 0) {
-            if (whole && !yg) {
-              fn[w] = got;
-              first = true;
-              if (!early && FUSE_COMMIT) {
-                s.visit[w] = vw | got;
-                msum += e - b;
+              bool first = got != 0;
+              if (got) {
+                if (yg)
+                  first = atomicOr((unsigned long long*)&fn[w], (unsigned long long)got) == 0ull;
+                else
+                  fn[w] = got;
               }
-            } else {
-              first = atomicOr((unsigned long long*)&fn[w], (unsigned long long)got) == 0ull;
+              list_append(first, w, &sctl[si].fl_n[nxt], s.fl[nxt]);
             }
+            t0 = grab_take(nx);
           }
-          list_append(first, w, &sctl[si].fl_n[nxt], s.fl[nxt]);
+        }
+        {
+          const int ntask = (int)((s.n_lanes + 31) / 32);
+          unsigned* cnt = &sctl[si].grab[2];
+          const int gsz = grab_size(ntask, nw);
+          int t0 = grab_take(grab_issue(cnt, gsz));
+          while (t0 < ntask) {
+            const unsigned nx = grab_issue(cnt, gsz);  // next tasks, in flight meanwhile
+            for (int task = t0; task < min(t0 + gsz, ntask); ++task) {
+              const int64_t i0 = (int64_t)task * 32;
+              const int64_t i = i0 + lane;
+              int32_t w = -1;
+              uint64_t got = 0;
+              if (i < s.n_lanes) {
+                w = BATCH_STREAM_LD(&s.lanes[i]);
+                const uint64_t vw = BATCH_STREAM_LD(&s.visit[w]);
+                const uint64_t miss = act & ~vw;
+                if (miss) {
+                  const int64_t rb = s.crow[w], re = s.crow[w + 1];
+                  got = hits_thread(s, fc, w, miss, 0ull, rb, re, w_pull);
+                  ++v_pull;
+                  if (got && !early && FUSE_COMMIT) {
+                    set_lane_levels(s, w, got, it1);
+                    s.visit[w] = vw | got;
+                    msum += re - rb;
+                  }
+                }
+              }
+              bool first = got != 0;
+              if (got) {
+                if (yg)
+                  first = atomicOr((unsigned long long*)&fn[w], (unsigned long long)got) == 0ull;
+                else
+                  fn[w] = got;
+              }
+              list_append(first, w, &sctl[si].fl_n[nxt], s.fl[nxt]);
+            }
+            t0 = grab_take(nx);
+          }
         }
         msum = warp_sum(msum);
         if (lane == 0 && msum) atomicAdd((unsigned long long*)&sctl[si].m_next, (unsigned long long)msum);
@@ -804,6 +860,7 @@ __global__ void __launch_bounds__(BT, 4)
         const int64_t nn = c.fl_n[nxt];
         c.fl_n[cur] = 0;
         c.q_n = 0;
+        c.grab[0] = c.grab[1] = c.grab[2] = 0;
         c.cur = nxt;
         c.iter = s_it[si] + 1;
         if (nn == 0 || c.iter >= 65534) {
