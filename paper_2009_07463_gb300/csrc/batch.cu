@@ -119,7 +119,7 @@ struct SlotCtl {
 #ifndef GRAB_ROUNDS
 #define GRAB_ROUNDS 8
 #endif
-constexpr int GRAB_MAX = 16;
+constexpr int GRAB_MAX = 4;
 __device__ __forceinline__ int grab_size(int ntask, int64_t nwarps) {
   return (int)max((int64_t)1, min((int64_t)GRAB_MAX, (int64_t)ntask / (nwarps * GRAB_ROUNDS)));
 }
