@@ -626,10 +626,6 @@ constexpr int LS = 2;
 // certainly not in the frontier, so the bitmap probe in L2 is only made for the rest: the
 // frontier itself and about F / 2^19 of the others (a second hash function lowered that
 // share but cost more instructions than it saved: 852-855 against 863-866 GTEPS at scale 26).
-// Windows of the streaming bottom-up step a warp takes per atomic on the control block's
-// counter (1: 855 GTEPS at scale 26, 2 and 4: 874, 8: 868, 16: 818; a fixed round-robin
-// share: 869).
-constexpr int WIN_TAKE = 4;
 constexpr int BLOOM_LOG = 19;
 constexpr int BLOOM_WORDS = (1 << BLOOM_LOG) / 32;
 constexpr int64_t BLOOM_MAX_FRONTIER = 65536;  // frontiers up to this size get a filter
@@ -902,16 +898,10 @@ __global__ void __launch_bounds__(T, MINB) bfs_bu_stream(BfsArgs a) {
   const uint32_t* bf = s_bloom;
   const uint64_t hi = (uint64_t)(uint32_t)(ctl->level + 1) << 32;
   const int lane = threadIdx.x & 31;
+  const int64_t gw = gtid() >> 5, nw = gthreads() >> 5;
   const int alone = max(a.bu_scan - 3, 0);  // CSR probes per lane and vertex after the record
   int64_t nf = 0, mf = 0, examined = 0;
-  // windows of BU_V bitmap words are handed out WIN_TAKE at a time from a counter in the
-  // control block (the cost of a window varies with its unvisited vertices' rows)
-  const int nwin = (int)((a.nwords + BU_V - 1) / BU_V);
-  int wt = (int)__shfl_sync(FULL, lane == 0 ? atomicAdd(&ctl->win_next, (unsigned)WIN_TAKE) : 0u, 0);
-  while (wt < nwin) {
-    const unsigned nx = lane == 0 ? atomicAdd(&ctl->win_next, (unsigned)WIN_TAKE) : 0u;  // in flight meanwhile
-    for (int wi = wt; wi < min(wt + WIN_TAKE, nwin); ++wi) {
-    const int64_t w0 = (int64_t)wi * BU_V;
+  for (int64_t w0 = gw * BU_V; w0 < a.nwords; w0 += nw * BU_V) {
     uint32_t vw[BU_V];
     int4 r[BU_V];  // prefix record; degree 0 for a visited vertex or one past n
 #pragma unroll
@@ -988,8 +978,6 @@ __global__ void __launch_bounds__(T, MINB) bfs_bu_stream(BfsArgs a) {
       const unsigned fb = __ballot_sync(FULL, fj);
       if (lane == j) vn[w0 + j] = vw[j] | fb;
     }
-    }
-    wt = (int)__shfl_sync(FULL, nx, 0);
   }
   block_commit<T / 32>(a, nf, mf, examined);
 }
@@ -1056,7 +1044,6 @@ __global__ void bfs_decide(BfsArgs a, cudaGraphConditionalHandle h_loop, cudaGra
     c->bu_stream = a.pre && !a.hub && (a.n - c->n_visited) * 6 > a.n;
     // a small frontier right after a top-down step (it is all in the queue): filter it
     c->bu_bloom = c->bu_stream && c->need_mark && nn <= BLOOM_MAX_FRONTIER;
-    c->win_next = 0;
     c->dir = nd;
   }
   if (use_handles) {
@@ -1112,7 +1099,6 @@ __device__ void ctl_begin(const BfsArgs& a, int32_t start, int32_t start_level, 
   c->bu_hash = 0;
   c->bu_stream = 0;
   c->bu_bloom = 0;
-  c->win_next = 0;
   c->alpha = alpha;
   c->beta = beta;
   c->force = force;

@@ -57,7 +57,6 @@ struct BfsCtl {
   int32_t bu_stream;  // 1: the bottom-up step streams all vertices (most are unvisited)
   int32_t bu_bloom;   // 1: ... and probes a shared-memory filter of a small frontier first
   int32_t nlevels;    // steps taken
-  uint32_t win_next;  // streaming bottom-up step: next window of bitmap words to hand out
   int64_t n_visited;  // vertices visited so far
   int64_t n_f;        // current frontier vertices
   int64_t m_f;        // their summed degree
