@@ -129,9 +129,11 @@ int bfs_common(gt_graph_t g, bool et, int64_t root, int32_t* parent, int32_t* le
 }
 
 // Copies one staged result (parent, level: n entries each) into page-locked host memory
-// from the SMs. A few CTAs writing over the host link reach its full rate (16 CTAs: 193
-// GB/s device to host on a GB300, the copy engine's rate there), and the copy then takes
-// the same path as the output pass's direct writes into host memory.
+// from the SMs, the same path as the output pass's direct writes into host memory. On its
+// own, 16 CTAs reach the host link's rate (193 GB/s device to host on a GB300, the copy
+// engine's rate there); beside the next root's traversal it needs more bytes in flight:
+// gt_bfs_roots at scale 26 gives 256 / 330 / 347-361 / 338 / 302 GTEPS with 16 / 32 /
+// 48-80 / 96 / 128 CTAs (more CTAs slow the traversal).
 __global__ void stage_to_host(const int32_t* __restrict__ sp, const int32_t* __restrict__ sl, int32_t* hp,
                               int32_t* hl, int64_t n, int vec) {
   const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, T = (int64_t)gridDim.x * blockDim.x;
@@ -145,7 +147,7 @@ __global__ void stage_to_host(const int32_t* __restrict__ sp, const int32_t* __r
     hl[i] = sl[i];
   }
 }
-constexpr int STAGE_COPY_CTAS = 32;
+constexpr int STAGE_COPY_CTAS = 64;
 
 // Device-accessible address of page-locked host memory, or null for pageable memory.
 void* pinned_device_ptr(void* p) {
