@@ -50,7 +50,6 @@ constexpr int CW = 4;  // 32-entry windows a warp keeps in flight on one adjacen
 // ones measured 0.7 % slower at scale 24.
 #define BATCH_STREAM_LD(p) __ldcs(p)
 
-constexpr bool FUSE_COMMIT = true;  // pulls commit the vertices they scan whole
 
 struct LaneInit {
   int32_t start;    // core id the lane's BFS starts from (-1: nothing to traverse)
@@ -116,9 +115,7 @@ struct SlotCtl {
 // barrier while others still hold work (with a fixed round-robin share, the last warp of a
 // scale-24 pull level finished 1.0-1.4 ms after the first). A take is about 1/GRAB_ROUNDS
 // of a warp's fair share, between 1 and GRAB_MAX tasks.
-#ifndef GRAB_ROUNDS
-#define GRAB_ROUNDS 8
-#endif
+constexpr int64_t GRAB_ROUNDS = 8;
 constexpr int GRAB_MAX = 4;
 __device__ __forceinline__ int grab_size(int ntask, int64_t nwarps) {
   return (int)max((int64_t)1, min((int64_t)GRAB_MAX, (int64_t)ntask / (nwarps * GRAB_ROUNDS)));
@@ -653,13 +650,13 @@ __global__ void __launch_bounds__(BT, 4)
               if (lane == 0 && (meta & BATCH_ITEM_FIRST)) ++v_pull;
               const uint64_t got = whole ? hits_warp<false>(s, fc, w, miss, 0ull, b, e, w_pull)
                                          : hits_warp<true>(s, fc, w, miss, 0ull, b, e, w_pull);
-              if (got && whole && !early && FUSE_COMMIT && lane < 8) set_lane_levels_q(s, w, got, it1, lane);
+              if (got && whole && !early && lane < 8) set_lane_levels_q(s, w, got, it1, lane);
               bool first = false;
               if (got && lane == 0) {
                 if (whole && !yg) {
                   fn[w] = got;
                   first = true;
-                  if (!early && FUSE_COMMIT) {
+                  if (!early) {
                     s.visit[w] = vw | got;
                     msum += e - b;
                   }
@@ -696,7 +693,7 @@ __global__ void __launch_bounds__(BT, 4)
                 }
               }
               if (__any_sync(FULL, d > 0)) got = hits_lanes32(s, fc, w, miss, rb, d, s_got[threadIdx.x >> 5], w_pull);
-              if (got && !early && FUSE_COMMIT) {
+              if (got && !early) {
                 set_lane_levels(s, w, got, it1);
                 s.visit[w] = vw | got;
                 msum += d;
@@ -733,7 +730,7 @@ __global__ void __launch_bounds__(BT, 4)
                   const int64_t rb = s.crow[w], re = s.crow[w + 1];
                   got = hits_thread(s, fc, w, miss, 0ull, rb, re, w_pull);
                   ++v_pull;
-                  if (got && !early && FUSE_COMMIT) {
+                  if (got && !early) {
                     set_lane_levels(s, w, got, it1);
                     s.visit[w] = vw | got;
                     msum += re - rb;

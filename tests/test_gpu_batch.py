@@ -230,3 +230,13 @@ def test_batch_large_core_medium_rows(torch):
     roots = graphgen.pick_roots(42, n, 64, og.degree()).tolist()
     (P,), (L,) = run_batch(torch, [g], [roots])
     check_rows(P, L, og, roots, "s21 large core")
+    # the same graph beside a small one (no medium list) in one launch: each slot takes
+    # its pull work from its own counters
+    ns = 1 << 12
+    es = graphgen.rmat_edges(12, 16, seed=43)
+    ogs = OracleGraph(es, ns)
+    gs = gt.gt_graph_build(es, ns)
+    rs = graphgen.pick_roots(44, ns, 70, ogs.degree()).tolist()
+    P2, L2 = run_batch(torch, [gs, g], [rs, roots[:40]])
+    check_rows(P2[0], L2[0], ogs, rs, "small graph beside s21")
+    check_rows(P2[1], L2[1], og, roots[:40], "s21 beside small graph")

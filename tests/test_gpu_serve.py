@@ -128,11 +128,14 @@ def test_destroy_with_queries_outstanding(torch, graphs):
     srv.destroy()  # finishes what is in flight, fails the rest, returns
 
 
-def test_roots_join_a_running_launch(torch):
+@pytest.mark.parametrize("scale", [18, 21])
+def test_roots_join_a_running_launch(torch, scale):
     # one root starts a batched launch; more roots of the same graph arrive while it runs
-    # and join its free lanes at a level boundary; every result equals gt_bfs alone
-    n = 1 << 18
-    e = graphgen.rmat_edges(18, 16, seed=91)
+    # and join its free lanes at a level boundary; every result equals gt_bfs alone (at
+    # scale 21 the core is large enough for the medium-row work list, which then also
+    # serves the joined lanes)
+    n = 1 << scale
+    e = graphgen.rmat_edges(scale, 16, seed=91)
     g = gt.gt_graph_build(e, n)
     cand = graphgen.pick_roots(92, n, 64, g.degree()).tolist()
     joined = 0
