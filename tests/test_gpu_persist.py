@@ -47,6 +47,31 @@ def test_save_load_round_trip(tmp_path, mh):
         assert np.array_equal(L[i].cpu().numpy(), wl) and np.array_equal(P[i].cpu().numpy(), wp)
 
 
+def test_save_load_large_core_batch(tmp_path):
+    """R-MAT scale 21 (core above 2^19 vertices, so its batched work lists include the
+    medium-row list): the loaded graph's batched traversal equals the saved graph's, bit
+    for bit."""
+    import torch
+    n = 1 << 21
+    e = graphgen.rmat_edges(21, 16, seed=54)
+    g = gt.gt_graph_build(e, n)
+    assert g.stats()["n_core"] >= 1 << 19
+    path = str(tmp_path / "g21.gtg")
+    gt.gt_graph_save(g, path)
+    h = gt.gt_graph_load(path)
+    roots = graphgen.pick_roots(55, n, 64, g.degree()).tolist()
+    outs = []
+    for x in (g, h):
+        P = torch.empty((len(roots), n), dtype=torch.int32, device="cuda")
+        L = torch.empty_like(P)
+        gt.gt_bfs_batch([x], [roots], [P], [L])
+        torch.cuda.synchronize()
+        outs.append((P, L))
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    g.free()
+    h.free()
+
+
 def test_load_refuses_damaged_files(tmp_path):
     import torch
     n = 1 << 10
