@@ -162,7 +162,7 @@ GT_API int gt_bfs(gt_graph_t g, int64_t root, int32_t* parent, int32_t* level, v
  * `stream`; root i writes parent[i] and level[i] (int32[n] each, both device or both host
  * memory; roots may differ). Host results are staged on the device (two staging pairs,
  * 16 B x n, allocated on first use and kept with the handle) and copied to the host on a
- * stream of the handle (by a 64-CTA copy kernel into page-locked memory, by the copy
+ * stream of the handle (by a 12-CTA copy kernel into page-locked memory, by the copy
  * engine into pageable memory) while the next root is traversed, so the host-link
  * transfer of one result overlaps the traversal of the next. Returns after
  * every host result is in place (device results: stream-ordered on `stream`). GT_EINVAL

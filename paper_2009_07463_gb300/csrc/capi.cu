@@ -129,25 +129,44 @@ int bfs_common(gt_graph_t g, bool et, int64_t root, int32_t* parent, int32_t* le
 }
 
 // Copies one staged result (parent, level: n entries each) into page-locked host memory
-// from the SMs, the same path as the output pass's direct writes into host memory. On its
-// own, 16 CTAs reach the host link's rate (193 GB/s device to host on a GB300, the copy
-// engine's rate there); beside the next root's traversal it needs more bytes in flight:
-// gt_bfs_roots at scale 26 gives 256 / 330 / 347-361 / 338 / 302 GTEPS with 16 / 32 /
-// 48-80 / 96 / 128 CTAs (more CTAs slow the traversal).
+// from the SMs, the same path as the output pass's direct writes into host memory. Beside
+// the next root's traversal the copy needs many bytes in flight but few CTAs, which would
+// otherwise slow that traversal: each thread keeps STAGE_COPY_UNROLL 16-byte pairs in
+// flight. gt_bfs_roots at scale 26, one pair in flight: 256 / 330 / 347-361 / 338 / 302
+// GTEPS with 16 / 32 / 48-80 / 96 / 128 CTAs; 4 in flight: 367-370 (16 CTAs), 357 (24);
+// 8 in flight: 372-374 with 8-16 CTAs.
+constexpr int STAGE_COPY_UNROLL = 8;
 __global__ void stage_to_host(const int32_t* __restrict__ sp, const int32_t* __restrict__ sl, int32_t* hp,
                               int32_t* hl, int64_t n, int vec) {
   const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, T = (int64_t)gridDim.x * blockDim.x;
   const int64_t n4 = vec ? n / 4 : 0;
-  for (int64_t i = t0; i < n4; i += T) {
-    reinterpret_cast<int4*>(hp)[i] = __ldcs(reinterpret_cast<const int4*>(sp) + i);
-    reinterpret_cast<int4*>(hl)[i] = __ldcs(reinterpret_cast<const int4*>(sl) + i);
+  const int4* sp4 = reinterpret_cast<const int4*>(sp);
+  const int4* sl4 = reinterpret_cast<const int4*>(sl);
+  for (int64_t i0 = t0; i0 < n4; i0 += T * STAGE_COPY_UNROLL) {
+    int4 a[STAGE_COPY_UNROLL], b[STAGE_COPY_UNROLL];
+#pragma unroll
+    for (int u = 0; u < STAGE_COPY_UNROLL; ++u) {
+      const int64_t i = i0 + u * T;
+      if (i < n4) {
+        a[u] = __ldcs(sp4 + i);
+        b[u] = __ldcs(sl4 + i);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < STAGE_COPY_UNROLL; ++u) {
+      const int64_t i = i0 + u * T;
+      if (i < n4) {
+        reinterpret_cast<int4*>(hp)[i] = a[u];
+        reinterpret_cast<int4*>(hl)[i] = b[u];
+      }
+    }
   }
   for (int64_t i = 4 * n4 + t0; i < n; i += T) {
     hp[i] = sp[i];
     hl[i] = sl[i];
   }
 }
-constexpr int STAGE_COPY_CTAS = 64;
+constexpr int STAGE_COPY_CTAS = 12;
 
 // Device-accessible address of page-locked host memory, or null for pageable memory.
 void* pinned_device_ptr(void* p) {
